@@ -1,0 +1,344 @@
+"""Benchmark: phi_l(-tau*A)v, l = 0..3, on the 3D convection-diffusion workload
+(A = A^x (+) A^y (+) A^z, A^d = -0.01*D2 + 1.0*D1_upwind on n = 128 points per dimension,
+2,097,152 unknowns, tau = 1e-2, v ~ U(-1,1) seed 0).
+
+One step = one phikron_apply (Algorithm 1 on 2^{-s}M plus s modified-squaring steps and
+phi_0) of a plan built once (the plan -- Algorithm 5, nodes, 1D exponentials -- is reused
+across steps as an exponential integrator reuses it across time steps; its time is
+reported separately as plan_ms).  Inputs are resident in HBM; L2 is flushed (a 512 MiB
+write) before every timed step.  value = unknowns processed per second over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32x3|ozaki]
+                    [--impl ours|reference] [--no-cpu-baseline]
+
+--impl reference times the oracle's CPU restatement of the same algorithm (numpy/scipy
+float64 on the host cores) on the same workload; it runs on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "phi_l(tau A)v unknowns/s at rel err<=1e-8 vs FP64 oracle; mixed vs FP64 GPU"
+UNIT = "unknowns/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "convdiff3d_n128_tau1e-2_seed0_samples.txt")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FLUSH_BYTES = 512 << 20
+
+PRECISIONS = {"fp64": (0, 1e-10), "tf32x3": (1, 1e-6), "ozaki": (2, 1e-10)}
+
+
+def workload(n=128):
+    return W.convdiff3d(n=n, tau=1e-2, l_max=3, tol=1e-10, seed=0)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def load_golden():
+    if not os.path.exists(GOLDEN):
+        return None
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    from make_convdiff_samples import load
+    return load(GOLDEN)
+
+
+def sampled_rel_err(out: np.ndarray, golden) -> list:
+    idx, vals, norm2, _ = golden
+    errs = []
+    for l in range(vals.shape[0]):
+        d = out[l][idx] - vals[l]
+        # sampled relative error, normalised like the full 2-norm error: rms(diff)/rms(phi_l)
+        errs.append(float(np.sqrt(np.mean(d * d)) / (norm2[l] / math.sqrt(out.shape[1]))))
+    return errs
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def roofline(info, prof, ms_per_step_profiled, precision):
+    """Roofline of the dominant kernel class from CUDA-event timings taken in bench.py."""
+    pk, src = peaks()
+    cls = max(prof["ms"], key=lambda k: prof["ms"][k])
+    launches = max(prof["launches"][cls], 1)
+    avg_ms = prof["ms"][cls] / launches
+    N, n = info["N"], info["n"]
+    actions = info["actions"]
+    flops_per_step = actions * 2.0 * N * sum(n[: info["dims"]])
+    if cls == "gemm_f64":
+        # float64 DFMA pipe: 152 SMs x 2 DFMA/clk (4 flop/clk/SM) x 2.07 GHz = 1.259 TFLOP/s
+        peak = 152 * 4 * 2.070e9 / 1e12
+        achieved = flops_per_step / (prof["ms"][cls] / prof["steps"] * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": "gemm_f64_kernel (DFMA mode products)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "nominal FP64 rate (152 SMs x 4 flop/clk x 2070 MHz)",
+                "avg_launch_ms": avg_ms, "launches_per_step": launches / prof["steps"],
+                "traffic": None}
+    if cls == "tc_mode":
+        # bytes that must move per mode pass: read + write the state once
+        bytes_step = prof.get("algorithmic_bytes", None)
+        hbm = pk.get("hbm_gbs", 6800.0)
+        achieved = bytes_step / (prof["ms"][cls] / prof["steps"] * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": "tc mode-product kernels", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": f"{src} hbm_gbs", "avg_launch_ms": avg_ms,
+                "launches_per_step": launches / prof["steps"], "traffic": None}
+    return {"bound": "hbm", "kernel": cls, "achieved": None, "peak": pk.get("hbm_gbs"),
+            "unit": "GB/s", "frac": None, "traffic": None}
+
+
+# ----------------------------------------------------------------------------- arms
+
+def cpu_reference_step(prob, v, s, m):
+    from oracle import quadrature as Q
+    return Q.alg6_phiquadmv(prob.factors, prob.tau, v, prob.l_max, prob.tol, s=s, m=m)
+
+
+def run_reference(args):
+    """The oracle's CPU restatement of Algorithms 1 and 6 (numpy/scipy float64), rank 0."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob = workload()
+    v = prob.vector()
+    from oracle import planner as PL
+    s, m, _ = PL.setup_quadrature(prob.tol, prob.l_max, PL.alpha_inf(prob.factors, prob.tau))
+    for _ in range(args.warmup):
+        cpu_reference_step(prob, v, s, m)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_reference_step(prob, v, s, m)
+    dt = (time.perf_counter() - t0) / args.steps
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    val = prob.N / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": prob.name, "N": prob.N, "l_max": 3,
+                                            "tau": 1e-2, "tol": prob.tol, "s": s, "m": m},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "full workload per step: oracle.quadrature.alg6_phiquadmv "
+                                       "(scipy expm + numpy tensordot mode products, float64)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2211_00696_gb300 as pk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    prec_id, tol = PRECISIONS[args.precision]
+    prob = workload()
+    v = prob.vector()
+    t0 = time.perf_counter()
+    plan = pk.Plan(prob.factors, prob.tau, prob.l_max, tol, precision=prec_id, device=local)
+    torch.cuda.synchronize()
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    info = plan.info()
+
+    V = torch.from_numpy(v).to(dev)
+    Out = torch.empty((prob.l_max + 1, prob.N), dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # accuracy on this run's output (sampled against stored oracle values)
+    plan.apply(V, Out)
+    torch.cuda.synchronize()
+    golden = load_golden()
+    errs = sampled_rel_err(Out.cpu().numpy(), golden) if golden is not None else None
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.apply(V, Out)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, each bracketed by CUDA events on the launching stream
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    plan.profile_begin(0)            # launch counting only
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        plan.apply(V, Out)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    counted = plan.profile_end()
+    clocks = clk.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot = float(np.sum(step_ms)) * 1e-3
+    if world > 1:
+        t = torch.tensor([tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+        dist.barrier()
+    ms_per_step = tot / args.steps * 1e3
+    value = world * prob.N * args.steps / tot
+    gpu_launches = int(sum(counted["launches"].values()))
+
+    # per-kernel CUDA-event timing of the same steps (separate pass, same stream)
+    plan.profile_begin(4096)
+    for i in range(args.steps):
+        flush.zero_()
+        plan.apply(V, Out)
+    torch.cuda.synchronize()
+    prof = plan.profile_end()
+    prof["steps"] = args.steps
+
+    # end to end through the public API with host buffers (pinned), copies inside the region
+    vh = torch.from_numpy(v).pin_memory()
+    oh = torch.empty((prob.l_max + 1, prob.N), dtype=torch.float64).pin_memory()
+    plan.apply_host_ptr(vh.data_ptr(), oh.data_ptr())
+    e2e_steps = max(3, min(args.steps, 10))
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.apply_host_ptr(vh.data_ptr(), oh.data_ptr())
+    e2e_s = (time.perf_counter() - te) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    line = None
+    if rank == 0:
+        dtype = {"fp64": "f64", "tf32x3": "f32(tf32x3 tensor)+f64", "ozaki": "bf16-slices+f64"}[args.precision]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": prob.name, "N": prob.N, "l_max": prob.l_max, "tau": prob.tau,
+                       "tol": tol, "precision": args.precision, "s": info["s"], "m": info["m"],
+                       "actions": info["actions"], "parallelism": f"replicas{world}",
+                       "l2": "flushed (512 MiB write) before every timed step"},
+            "rel_err_sampled": errs,
+            "plan_ms": plan_ms,
+            "wall_s_timed": wall,
+            "gpu_launches": gpu_launches,
+            "launches_by_class": counted["launches"],
+            "kernel_ms_per_step": {k: v_ / args.steps for k, v_ in prof["ms"].items() if v_ > 0},
+            "roofline": roofline(info, prof, None, args.precision),
+            "clocks": clocks,
+            "e2e": {"value": world * prob.N / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": prob.N * 8, "d2h_bytes_per_step": (prob.l_max + 1) * prob.N * 8},
+        }
+        if args.cpu_baseline and world == 1:
+            from oracle import planner as PL
+            s, m, _ = PL.setup_quadrature(prob.tol, prob.l_max, PL.alpha_inf(prob.factors, prob.tau))
+            tc = time.perf_counter()
+            cpu_reference_step(prob, v, s, m)
+            dt = time.perf_counter() - tc
+            cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+            line["cpu_baseline"] = {"value": prob.N / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": "one full step: oracle.quadrature.alg6_phiquadmv (same "
+                                              "algorithm, numpy/scipy float64, BLAS threads = cores)"}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

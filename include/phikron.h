@@ -1,0 +1,212 @@
+/*
+ * phikron -- actions of phi-functions of Kronecker-sum matrices on one GB300 GPU.
+ *
+ * Computes Out[l] = phi_l(-tau*A) v for l = 0..l_max, where
+ *   A = A^x (+) A^y            (2D)   or   A = A^x (+) A^y (+) A^z   (3D)
+ * is a Kronecker sum of small dense 1D factors (Croci & Munoz-Matute, arXiv 2211.00696,
+ * Sec. 2.2, Eq. (6)), phi_0(M) = e^M and phi_p(M) = int_0^1 e^{(1-t)M} t^{p-1}/(p-1)! dt
+ * (Sec. 2.1, Eq. (3)).  The method is Gauss-Legendre quadrature of that integral on the
+ * scaled matrix 2^{-s}M (Sec. 3.1, Algorithm 1), followed by s steps of the modified
+ * squaring identity (Sec. 3.3, Eq. (29), Algorithm 6); every quadrature node needs only
+ * 1D matrix exponentials applied mode by mode (Eq. (7)-(8)), so A is never assembled.
+ * The scaling s and node count m come from the a-priori bound of Theorem 3.2 through
+ * Algorithms 3-5 (Sec. 3.2-3.3).
+ *
+ * Conventions shared by every entry point:
+ *   - Vectors are float64, C-order [n_x][n_y][n_z] (z fastest).  The first factor acts on
+ *     the slowest axis, matching the Kronecker ordering of Eq. (6).
+ *   - Factor matrices are float64, row-major, n_d x n_d, on the HOST; they are copied.
+ *   - "device" pointers are CUDA device (or managed) memory on the plan's device.
+ *   - Streams are passed as void* and are cudaStream_t values (NULL = legacy default).
+ *   - Every function returns PHIKRON_OK (0) or a negative PHIKRON_E* code and never
+ *     aborts the process; phikron_last_error() then gives a message (thread-local).
+ *   - Nothing here is thread-safe with respect to one plan: use one plan per host thread
+ *     or serialise calls on a plan.
+ */
+#ifndef PHIKRON_H
+#define PHIKRON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ error codes */
+#define PHIKRON_OK              0
+#define PHIKRON_EINVAL         -1  /* bad argument: sizes, NaN/Inf, tol <= 0, null pointer ... */
+#define PHIKRON_ENOMEM         -2  /* host or device allocation failed                          */
+#define PHIKRON_ECUDA          -3  /* a CUDA runtime/driver call failed                         */
+#define PHIKRON_ETIMEOUT       -4  /* a bounded device wait gave up (device status word)        */
+#define PHIKRON_ENOTCONVERGED  -5  /* planner root finding failed (Theorem 3.2 quartic)         */
+#define PHIKRON_ENOTSUP        -6  /* option combination not built                              */
+
+/* ------------------------------------------------------------------ options */
+#define PHIKRON_QUAD_GAUSS        0   /* Gauss-Legendre, Algorithm 1 (Sec. 3.1)            */
+#define PHIKRON_QUAD_CC           1   /* Clenshaw-Curtis nodes with the CC bound            */
+
+#define PHIKRON_PREC_FP64         0   /* every product in float64 (DFMA)                    */
+#define PHIKRON_PREC_TF32X3       1   /* mode products as 3 TF32 tensor-core passes (hi*hi +
+                                         hi*lo + lo*hi), FP32 accumulate; float64 expms,
+                                         weights and squaring recurrence                    */
+#define PHIKRON_PREC_OZAKI_BF16   2   /* mode products as exact BF16 slice products (Ozaki
+                                         splitting), combined in float64                    */
+
+#define PHIKRON_SELECT_PAPER      0   /* (s, m) from Algorithm 5                            */
+#define PHIKRON_SELECT_MLP        1   /* (s, m) from the learned selector, Algorithm 5 as
+                                         fallback (see phikron_selector_*)                  */
+
+typedef struct phikron_opts {
+  int    quad;        /* PHIKRON_QUAD_*; default GAUSS                                        */
+  int    precision;   /* PHIKRON_PREC_*; default FP64                                         */
+  int    selector;    /* PHIKRON_SELECT_*; default PAPER                                      */
+  int    force_s;     /* >= 0 overrides the scaling exponent s (paper's l); default -1        */
+  int    force_m;     /* >= 1 overrides the number of nodes m (paper's n+1); default -1       */
+  double alpha;       /* > 0 overrides ||tau*A||_inf estimate; default: Eq. (31) bound        */
+  double beta;        /* > 0 overrides beta of Algorithm 3; default 1 (tol relative to
+                         ||v||_inf)                                                         */
+  int    device;      /* CUDA device ordinal; -1 = the calling thread's current device        */
+  int    max_rhs;     /* largest nrhs passed to phikron_apply_many; default 1                 */
+} phikron_opts;
+
+/* Fills *opts with the defaults listed above. */
+void phikron_opts_default(phikron_opts* opts);
+
+/* ------------------------------------------------------------------ plans */
+typedef struct phikron_plan_s* phikron_plan_t;
+
+/*
+ * phikron_plan -- build everything that does not depend on v (Algorithm 6, first step):
+ * alpha = tau*sum_d ||A^d||_inf (Eq. (31)); (s, m) = setup_quadrature(tol, l_max, alpha,
+ * beta) (Algorithm 5); Gauss-Legendre nodes x_k and weights w_k on [0,1]; the node
+ * weights c_{j,k} = w_k x_k^{j-1}/(j-1)!; and on the device every 1D exponential the
+ * apply needs: E_{k,d} = exp((1-x_k) 2^{-s} M^d) and G_{t,d} = exp(2^{t-s} M^d),
+ * t = 0..s, with M^d = -tau*A^d (batched float64 Pade [13/13] scaling and squaring).
+ *
+ *   out    : receives the plan (owned by the library; free with phikron_destroy).
+ *   dims   : 2 or 3.
+ *   A      : dims HOST pointers; A[d] is n[d] x n[d], row-major float64.  Copied.
+ *   n      : dims sizes, 1 <= n[d] <= 4096.
+ *   tau    : time step, finite; phi_l(-tau*A) is computed (tau may be 0).
+ *   l_max  : highest order, 0 <= l_max <= 20 (Out holds l_max+1 vectors).
+ *   tol    : quadrature tolerance relative to ||v||_inf, 1e-16 <= tol < 1.
+ *   opts   : may be NULL (defaults).
+ * Errors: EINVAL (arguments, NaN/Inf entries), ENOMEM, ECUDA, ENOTCONVERGED, ENOTSUP.
+ * Synchronous: returns after the device exponentials are complete.
+ */
+int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const int* n,
+                 double tau, int l_max, double tol, const phikron_opts* opts);
+
+/*
+ * phikron_apply -- Out[l*N + i] = phi_l(-tau*A) v [i], l = 0..l_max, N = prod n[d]
+ * (Algorithm 1 on 2^{-s}M, then s modified-squaring steps of Eq. (29); phi_0 by Eq. (8)).
+ *   V   : DEVICE pointer, N float64.  Out: DEVICE pointer, (l_max+1)*N float64; must not
+ *         overlap V.  Both owned by the caller.
+ *   stream : cudaStream_t; the call is asynchronous on it and allocates nothing.
+ * Errors: EINVAL (null plan/pointers), ECUDA (launch failure).  Calls on one plan that
+ * overlap on the GPU race on the plan's work buffers: serialise them on one stream.
+ */
+int phikron_apply(phikron_plan_t plan, const double* V, double* Out, void* stream);
+
+/*
+ * phikron_apply_many -- nrhs independent right-hand sides in one call.
+ *   V   : DEVICE, nrhs*N float64 (right-hand side r at V + r*N).
+ *   Out : DEVICE, nrhs*(l_max+1)*N float64 (rhs r, order l at Out + (r*(l_max+1)+l)*N).
+ *   1 <= nrhs <= opts.max_rhs given at plan time.
+ */
+int phikron_apply_many(phikron_plan_t plan, int nrhs, const double* V, double* Out, void* stream);
+
+/*
+ * phikron_apply_host -- phikron_apply with HOST buffers: copies V (N float64) to the
+ * plan's device staging buffer, applies, copies the (l_max+1)*N results back into Out.
+ * Synchronous (returns when Out is filled).  Pinned host memory makes the copies faster.
+ */
+int phikron_apply_host(phikron_plan_t plan, const double* V_host, double* Out_host, void* stream);
+
+typedef struct phikron_info {
+  int    dims, n[3];
+  int64_t N;
+  int    l_max;
+  int    s;            /* scaling exponent (paper's l)                                  */
+  int    m;            /* number of quadrature nodes (paper's n+1)                      */
+  int    cost;         /* m + s*l_max, Algorithm 5's C with c1 = 0, c2 = 1              */
+  int    actions;      /* Kronecker actions per apply: m + s*l_max + 1 (phi_0)          */
+  double alpha;        /* ||tau*A||_inf estimate used                                   */
+  double log10_bound;  /* log10 of Algorithm 3's bound at the chosen (s, m)             */
+  int    precision, quad, selector_used;
+  int    unique_factors;
+  size_t device_bytes; /* device memory held by the plan                                */
+} phikron_info;
+
+int  phikron_plan_info(phikron_plan_t plan, phikron_info* info);
+
+/* Copies the quadrature nodes and weights on [0,1] (m each) to HOST memory. */
+int  phikron_plan_nodes(phikron_plan_t plan, double* x, double* w);
+
+void phikron_destroy(phikron_plan_t plan);
+
+/* ------------------------------------------------------------------ per-kernel timing
+ * Between phikron_profile_begin and phikron_profile_end every kernel the plan's applies
+ * launch is counted by class, and (if max_timed > 0) the first max_timed launches are
+ * bracketed by CUDA events recorded on the launch stream.  profile_end synchronises on
+ * those events and reports, per class, the launches and the summed event time in ms.
+ * Classes: 0 float64 mode-product GEMM, 1 node-weighted sums, 2 squaring combination,
+ * 3 tensor-core mode products, 4 precision conversions, 5 other.
+ */
+#define PHIKRON_KERNEL_CLASSES 6
+typedef struct phikron_profile {
+  double    ms[PHIKRON_KERNEL_CLASSES];
+  long long launches[PHIKRON_KERNEL_CLASSES];
+  long long timed_launches;
+} phikron_profile;
+
+int phikron_profile_begin(phikron_plan_t plan, int max_timed);
+int phikron_profile_end(phikron_plan_t plan, phikron_profile* out);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char* phikron_last_error(void);
+
+/* ------------------------------------------------------------------ planner (host only)
+ * Algorithms 3-5 of Sec. 3.2-3.3, exposed so the planner can be checked without a GPU.
+ * rule: PHIKRON_QUAD_GAUSS or PHIKRON_QUAD_CC.
+ */
+
+/* log of Algorithm 3's bound quaderr(n, p, alpha, beta) for continuous n >= 2. */
+int phikron_log_quaderr(double n, int p, double alpha, double beta, int rule, double* log_err);
+
+/* Algorithm 4: smallest integer n with quaderr(n) <= eps (the rule has n+1 nodes). */
+int phikron_quadnodes(double eps, int p, double alpha, double beta, int rule, int* n);
+
+/* Algorithm 5: optimal scaling s (paper's l), nodes m = n+1 and cost m + s*p. */
+int phikron_setup_quadrature(double eps, int p, double alpha, double beta, int rule,
+                             int* s, int* m, int* cost);
+
+/* m-point Gauss-Legendre rule on [0,1] (Newton on the Legendre recurrence), 1 <= m <= 256. */
+int phikron_gauss_legendre(int m, double* x, double* w);
+
+/* (n+1)-point Clenshaw-Curtis rule on [0,1], 1 <= n <= 512. */
+int phikron_clenshaw_curtis(int n, double* x, double* w);
+
+/* ------------------------------------------------------------------ device building blocks
+ * Exposed for testing the kernels in isolation; all pointers DEVICE, asynchronous.
+ */
+
+/* E[b] = exp(scale[b] * A[b]) for count matrices of size n x n (row-major, contiguous),
+ * float64 Pade scaling and squaring (Higham 2005).  scale is a HOST array of count
+ * doubles; norms1 is a HOST array with ||A[b]||_1 (used to pick degree and scaling
+ * without a device round trip).  workspace: DEVICE, at least
+ * phikron_expm_workspace_bytes(count, n) bytes. */
+size_t phikron_expm_workspace_bytes(int count, int n);
+int phikron_expm_batched(int count, int n, const double* A, const double* scale,
+                         const double* norms1, double* E, void* workspace, void* stream);
+
+/* Out = (E_1 (x) ... (x) E_dims) V for one vector, float64 (mode products, Eq. (8)).
+ * E: dims DEVICE pointers to n[d] x n[d] row-major matrices; work: DEVICE, N doubles. */
+int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const double* V,
+                           double* Out, double* work, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHIKRON_H */

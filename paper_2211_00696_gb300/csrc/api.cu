@@ -1,0 +1,540 @@
+// C ABI of libphikron: plan construction (Algorithm 6's set-up) and the apply path
+// (Algorithm 1 on 2^{-s}M, s modified-squaring steps of Eq. (29), phi_0 by Eq. (8)).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "plan.h"
+
+namespace phikron {
+
+thread_local Profiler* tl_prof = nullptr;
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+void clear_error() { g_err.clear(); }
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  int rc = PHIKRON_OK;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      rc = PHIKRON_ECUDA;
+      set_error("cudaGetDevice failed (no CUDA device?)");
+      return;
+    }
+    if (dev >= 0 && dev != prev) {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        rc = PHIKRON_ECUDA;
+        set_error("cudaSetDevice failed");
+        return;
+      }
+      changed = true;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+double norm_inf(const double* a, int n) {
+  double best = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += std::fabs(a[(size_t)i * n + j]);
+    best = std::max(best, s);
+  }
+  return best;
+}
+
+double norm_one(const double* a, int n) {
+  double best = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += std::fabs(a[(size_t)i * n + j]);
+    best = std::max(best, s);
+  }
+  return best;
+}
+
+}  // namespace
+
+Plan::~Plan() {
+  for (void* p : allocations) cudaFree(p);
+}
+
+int Plan::alloc(void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    return PHIKRON_ENOMEM;
+  }
+  allocations.push_back(*p);
+  device_bytes += bytes;
+  return PHIKRON_OK;
+}
+
+// ----------------------------------------------------------------------------- plan
+
+int build_plan(Plan& P, int dims, const double* const* A, const int* n, double tau, int l_max,
+               double tol, const phikron_opts& o) {
+  P.dims = dims;
+  P.tau = tau;
+  P.p = l_max;
+  P.tol = tol;
+  P.opts = o;
+  P.N = 1;
+  for (int d = 0; d < dims; ++d) {
+    P.n[d] = n[d];
+    P.N *= n[d];
+  }
+  for (int d = dims; d < 3; ++d) P.n[d] = 1;
+
+  // alpha = tau * sum_d ||A^d||_inf  (Eq. (31))
+  double alpha = 0.0;
+  std::vector<double> n1(dims);
+  for (int d = 0; d < dims; ++d) {
+    alpha += std::fabs(tau) * norm_inf(A[d], n[d]);
+    n1[d] = norm_one(A[d], n[d]);
+  }
+  if (o.alpha > 0.0) alpha = o.alpha;
+  P.alpha = alpha;
+  const double beta = (o.beta > 0.0) ? o.beta : 1.0;
+  P.log10_bound = -INFINITY;
+
+  // (s, m): Algorithm 5, unless forced or trivial
+  int s = 0, m = 0, cost = 0;
+  if (l_max >= 1) {
+    if (alpha > 0.0) {
+      PK_RET(planner::setup_quadrature(tol, l_max, alpha, beta, o.quad, &s, &m, &cost));
+    } else {
+      s = 0;
+      m = (l_max + 1) / 2 + 1;  // M = 0: the integrand is a polynomial of degree l_max-1
+    }
+    if (o.force_s >= 0) s = o.force_s;
+    if (o.force_m >= 1) m = o.force_m;
+    if (o.quad == PHIKRON_QUAD_CC && m < 2) m = 2;
+    if (m > 256 || s > 60) {
+      set_error("plan: node count or scaling out of range (m <= 256, s <= 60)");
+      return PHIKRON_EINVAL;
+    }
+    if (alpha > 0.0) {
+      double lb;
+      if (planner::log_quaderr(std::max(1.0, (double)(m - 1)), l_max, std::ldexp(alpha, -s), beta,
+                               o.quad, &lb) == PHIKRON_OK)
+        P.log10_bound = lb / std::log(10.0);
+      clear_error();
+    }
+  }
+  P.s = s;
+  P.m = m;
+  P.cost = m + s * l_max;
+
+  // quadrature rule and node weights c_{j,k} = w_k x_k^{j-1}/(j-1)!  (Algorithm 1)
+  P.x.assign(m, 0.0);
+  P.w.assign(m, 0.0);
+  if (m > 0) {
+    if (o.quad == PHIKRON_QUAD_GAUSS)
+      PK_RET(planner::gauss_legendre(m, P.x.data(), P.w.data()));
+    else
+      PK_RET(planner::clenshaw_curtis(m - 1, P.x.data(), P.w.data()));
+  }
+  P.coef.assign((size_t)std::max(1, l_max) * std::max(1, m), 0.0);
+  for (int j = 1; j <= l_max; ++j) {
+    double fact = 1.0;
+    for (int q = 2; q <= j - 1; ++q) fact *= q;
+    for (int k = 0; k < m; ++k) P.coef[(size_t)(j - 1) * m + k] = P.w[k] * std::pow(P.x[k], j - 1) / fact;
+  }
+
+  // unique factors (bitwise-equal matrices share their exponentials)
+  P.nuniq = 0;
+  for (int d = 0; d < dims; ++d) {
+    int found = -1;
+    for (int u = 0; u < P.nuniq; ++u) {
+      const int dd = P.uniq_rep[u];
+      if (n[dd] == n[d] && std::memcmp(A[dd], A[d], sizeof(double) * (size_t)n[d] * n[d]) == 0) {
+        found = u;
+        break;
+      }
+    }
+    if (found < 0) {
+      found = P.nuniq++;
+      P.uniq_rep[found] = d;
+    }
+    P.uniq_of[d] = found;
+  }
+
+  // device: 1D exponentials per unique factor, layout [nodes 0..m-1 | G_s | G_0..G_{s-1}]
+  P.nexp = m + 1 + s;
+  cudaStream_t st = nullptr;
+  for (int u = 0; u < P.nuniq; ++u) {
+    const int d = P.uniq_rep[u];
+    const int nd = n[d];
+    const size_t nn = (size_t)nd * nd;
+    const int cnt = m + 1 + (s > 0 ? 1 : 0);  // nodes, exp(M), G_0
+    double* dExp = nullptr;
+    PK_RET(P.alloc((void**)&dExp, sizeof(double) * nn * P.nexp));
+    P.dExp[u] = dExp;
+    double* dIn = nullptr;
+    void* ws = nullptr;
+    double* dOut = nullptr;
+    PK_RET(P.alloc((void**)&dIn, sizeof(double) * nn * cnt));
+    PK_RET(P.alloc((void**)&dOut, sizeof(double) * nn * cnt));
+    PK_RET(P.alloc(&ws, expm_workspace_bytes(cnt, nd)));
+    for (int c = 0; c < cnt; ++c)
+      PK_TRY_CUDA(cudaMemcpy(dIn + c * nn, A[d], sizeof(double) * nn, cudaMemcpyHostToDevice));
+    std::vector<double> scale(cnt), norms(cnt, n1[d]);
+    const double sc = -tau * std::ldexp(1.0, -s);
+    for (int k = 0; k < m; ++k) scale[k] = sc * (1.0 - P.x[k]);
+    scale[m] = -tau;  // exp(M^d) for phi_0
+    if (s > 0) scale[m + 1] = sc;  // G_0 = exp(2^{-s} M^d)
+    PK_RET(expm_batched(cnt, nd, dIn, scale.data(), norms.data(), dOut, ws, st));
+    PK_TRY_CUDA(cudaMemcpyAsync(dExp, dOut, sizeof(double) * nn * (m + 1), cudaMemcpyDeviceToDevice, st));
+    if (s > 0) {
+      PK_TRY_CUDA(cudaMemcpyAsync(dExp + (size_t)(m + 1) * nn, dOut + (size_t)(m + 1) * nn,
+                                  sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+      // G_{t+1} = G_t^2  (Algorithm 6, step 2 of the squaring loop)
+      for (int t = 0; t + 1 < s; ++t) {
+        GemmF64 g{};
+        const double* Gt = dExp + (size_t)(m + 1 + t) * nn;
+        double* Gn = dExp + (size_t)(m + 2 + t) * nn;
+        g.A = Gt; g.sAm = nd; g.sAk = 1;
+        g.B = Gt; g.sBk = nd; g.sBn = 1;
+        g.C = Gn; g.sCm = nd; g.sCn = 1;
+        g.M = g.N = g.K = nd; g.nb = 1; g.nb0 = 1; g.alpha = 1.0; g.beta = 0.0;
+        PK_RET(gemm_f64(g, st));
+      }
+    }
+    PK_TRY_CUDA(cudaStreamSynchronize(st));
+    // staging for the expm is no longer needed
+    for (void* q : {(void*)dIn, (void*)dOut, ws}) {
+      cudaFree(q);
+      P.allocations.erase(std::find(P.allocations.begin(), P.allocations.end(), q));
+    }
+    P.device_bytes -= sizeof(double) * nn * cnt * 2 + expm_workspace_bytes(cnt, nd);
+  }
+
+  // node weights on the device
+  PK_RET(P.alloc((void**)&P.dCoef, sizeof(double) * P.coef.size()));
+  PK_TRY_CUDA(cudaMemcpy(P.dCoef, P.coef.data(), sizeof(double) * P.coef.size(), cudaMemcpyHostToDevice));
+
+  // apply work buffers
+  const long long N = P.N;
+  const int nv = std::max(m + 1, std::max(l_max, 1));
+  PK_RET(P.alloc((void**)&P.dW1, sizeof(double) * (size_t)nv * N));
+  PK_RET(P.alloc((void**)&P.dW2, sizeof(double) * (size_t)nv * N));
+  PK_RET(P.alloc((void**)&P.dY, sizeof(double) * (size_t)std::max(l_max, 1) * N));
+  PK_RET(P.alloc((void**)&P.dYn, sizeof(double) * (size_t)std::max(l_max, 1) * N));
+  PK_RET(P.alloc((void**)&P.dV, sizeof(double) * (size_t)N));
+  PK_RET(P.alloc((void**)&P.dOut, sizeof(double) * (size_t)(l_max + 1) * N));
+  PK_RET(precision_setup(P));
+  return PHIKRON_OK;
+}
+
+// (x)_d E_d applied to `nvec` vectors, each with its own matrices (E_stride matrices apart
+// in the per-factor exponential arrays, starting at index e0) or shared ones (E_stride 0).
+// src -> ... -> result; returns the buffer holding the result.
+int kron_chain_f64(const Plan& P, const double* src, long long src_sb, int nvec, int e0, int e_stride,
+                   double* bufA, double* bufB, double* final_dst, cudaStream_t st) {
+  const long long N = P.N;
+  const double* cur = src;
+  long long cur_sb = src_sb;
+  for (int d = 0; d < P.dims; ++d) {
+    long long B0 = 1, R = 1;
+    for (int q = 0; q < d; ++q) B0 *= P.n[q];
+    for (int q = d + 1; q < P.dims; ++q) R *= P.n[q];
+    const int nd = P.n[d];
+    const size_t nn = (size_t)nd * nd;
+    const double* E = P.dExp[P.uniq_of[d]] + (size_t)e0 * nn;
+    double* dst = (d == P.dims - 1) ? final_dst : ((d % 2 == 0) ? bufA : bufB);
+    PK_RET(mode_product_f64(cur, cur_sb, dst, N, E, (long long)e_stride * nn, nvec, B0, nd, R, st));
+    cur = dst;
+    cur_sb = N;
+  }
+  return PHIKRON_OK;
+}
+
+int apply_f64(Plan& P, const double* V, double* Out, cudaStream_t st) {
+  const long long N = P.N;
+  const int p = P.p, m = P.m, s = P.s;
+  if (p == 0) {
+    // phi_0 only: (x)_d exp(M^d) v
+    return kron_chain_f64(P, V, 0, 1, m, 0, P.dW1, P.dW2, Out, st);
+  }
+  // node phase: m node actions + phi_0 in one batched chain (v shared: stride 0)
+  PK_RET(kron_chain_f64(P, V, 0, m + 1, 0, 1, P.dW1, P.dW2,
+                        (P.dims % 2 == 1) ? P.dW1 : P.dW2, st));
+  const double* T = (P.dims % 2 == 1) ? P.dW1 : P.dW2;
+  // the chain's last destination is the buffer given; use a dedicated one to avoid aliasing
+  PK_TRY_CUDA(cudaMemcpyAsync(Out, T + (size_t)m * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  double* Y = (s == 0) ? Out + N : P.dY;
+  PK_RET(weighted_sum_f64(T, N, P.dCoef, p, m, N, Y, N, st));
+  double* Yn = P.dYn;
+  for (int t = 0; t < s; ++t) {
+    // Z_i = (x)_d G_{t,d} y_i for i = 1..p (shared matrices)
+    double* Z = (P.dims % 2 == 1) ? P.dW1 : P.dW2;
+    PK_RET(kron_chain_f64(P, Y, N, p, m + 1 + t, 0, P.dW1, P.dW2, Z, st));
+    double* dst = (t == s - 1) ? Out + N : Yn;
+    PK_RET(squaring_combine_f64(Z, Y, dst, p, N, N, st));
+    Yn = Y;
+    Y = dst;
+  }
+  return PHIKRON_OK;
+}
+
+}  // namespace phikron
+
+// =============================================================================== C ABI
+using namespace phikron;
+
+struct phikron_plan_s {
+  Plan impl;
+};
+
+extern "C" {
+
+void phikron_opts_default(phikron_opts* o) {
+  if (!o) return;
+  o->quad = PHIKRON_QUAD_GAUSS;
+  o->precision = PHIKRON_PREC_FP64;
+  o->selector = PHIKRON_SELECT_PAPER;
+  o->force_s = -1;
+  o->force_m = -1;
+  o->alpha = 0.0;
+  o->beta = 0.0;
+  o->device = -1;
+  o->max_rhs = 1;
+}
+
+const char* phikron_last_error(void) { return g_err.c_str(); }
+
+int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const int* n, double tau,
+                 int l_max, double tol, const phikron_opts* opts) {
+  clear_error();
+  if (!out) { set_error("phikron_plan: out is NULL"); return PHIKRON_EINVAL; }
+  *out = nullptr;
+  if (dims != 2 && dims != 3) { set_error("phikron_plan: dims must be 2 or 3"); return PHIKRON_EINVAL; }
+  if (!A || !n) { set_error("phikron_plan: A or n is NULL"); return PHIKRON_EINVAL; }
+  if (!std::isfinite(tau)) { set_error("phikron_plan: tau must be finite"); return PHIKRON_EINVAL; }
+  if (l_max < 0 || l_max > 20) { set_error("phikron_plan: l_max must be in 0..20"); return PHIKRON_EINVAL; }
+  if (!(tol >= 1e-16 && tol < 1.0)) { set_error("phikron_plan: tol must be in [1e-16, 1)"); return PHIKRON_EINVAL; }
+  long long N = 1;
+  for (int d = 0; d < dims; ++d) {
+    if (!A[d]) { set_error("phikron_plan: factor pointer is NULL"); return PHIKRON_EINVAL; }
+    if (n[d] < 1 || n[d] > 4096) { set_error("phikron_plan: n[d] must be in 1..4096"); return PHIKRON_EINVAL; }
+    for (long long i = 0; i < (long long)n[d] * n[d]; ++i)
+      if (!std::isfinite(A[d][i])) { set_error("phikron_plan: factor has NaN/Inf"); return PHIKRON_EINVAL; }
+    N *= n[d];
+  }
+  if (N > (1LL << 31)) { set_error("phikron_plan: N = prod n[d] must be <= 2^31"); return PHIKRON_EINVAL; }
+  phikron_opts o;
+  phikron_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.quad != PHIKRON_QUAD_GAUSS && o.quad != PHIKRON_QUAD_CC) { set_error("phikron_plan: bad quad"); return PHIKRON_EINVAL; }
+  if (o.precision < PHIKRON_PREC_FP64 || o.precision > PHIKRON_PREC_OZAKI_BF16) { set_error("phikron_plan: bad precision"); return PHIKRON_EINVAL; }
+  if (o.max_rhs < 1) o.max_rhs = 1;
+  if (o.selector != PHIKRON_SELECT_PAPER) {
+    set_error("phikron_plan: selector MLP needs phikron_plan_select (not in this entry point)");
+    return PHIKRON_ENOTSUP;
+  }
+  DeviceGuard dg(o.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  if (cudaGetDevice(&o.device) != cudaSuccess) { set_error("cudaGetDevice failed"); return PHIKRON_ECUDA; }
+  phikron_plan_s* h = new (std::nothrow) phikron_plan_s();
+  if (!h) { set_error("phikron_plan: host allocation failed"); return PHIKRON_ENOMEM; }
+  int rc = build_plan(h->impl, dims, A, n, tau, l_max, tol, o);
+  if (rc != PHIKRON_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return PHIKRON_OK;
+}
+
+int phikron_apply(phikron_plan_t plan, const double* V, double* Out, void* stream) {
+  clear_error();
+  if (!plan || !V || !Out) { set_error("phikron_apply: NULL argument"); return PHIKRON_EINVAL; }
+  Plan& P = plan->impl;
+  DeviceGuard dg(P.opts.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  ProfScope ps(&P.prof);
+  return apply_dispatch(P, 1, V, Out, static_cast<cudaStream_t>(stream));
+}
+
+int phikron_apply_many(phikron_plan_t plan, int nrhs, const double* V, double* Out, void* stream) {
+  clear_error();
+  if (!plan || !V || !Out) { set_error("phikron_apply_many: NULL argument"); return PHIKRON_EINVAL; }
+  Plan& P = plan->impl;
+  if (nrhs < 1 || nrhs > P.opts.max_rhs) { set_error("phikron_apply_many: nrhs out of range"); return PHIKRON_EINVAL; }
+  DeviceGuard dg(P.opts.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  ProfScope ps(&P.prof);
+  return apply_dispatch(P, nrhs, V, Out, static_cast<cudaStream_t>(stream));
+}
+
+int phikron_apply_host(phikron_plan_t plan, const double* V_host, double* Out_host, void* stream) {
+  clear_error();
+  if (!plan || !V_host || !Out_host) { set_error("phikron_apply_host: NULL argument"); return PHIKRON_EINVAL; }
+  Plan& P = plan->impl;
+  DeviceGuard dg(P.opts.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PK_TRY_CUDA(cudaMemcpyAsync(P.dV, V_host, sizeof(double) * P.N, cudaMemcpyHostToDevice, st));
+  {
+    ProfScope ps(&P.prof);
+    PK_RET(apply_dispatch(P, 1, P.dV, P.dOut, st));
+  }
+  PK_TRY_CUDA(cudaMemcpyAsync(Out_host, P.dOut, sizeof(double) * P.N * (P.p + 1), cudaMemcpyDeviceToHost, st));
+  PK_TRY_CUDA(cudaStreamSynchronize(st));
+  return PHIKRON_OK;
+}
+
+int phikron_plan_info(phikron_plan_t plan, phikron_info* info) {
+  clear_error();
+  if (!plan || !info) { set_error("phikron_plan_info: NULL argument"); return PHIKRON_EINVAL; }
+  const Plan& P = plan->impl;
+  std::memset(info, 0, sizeof(*info));
+  info->dims = P.dims;
+  for (int d = 0; d < 3; ++d) info->n[d] = P.n[d];
+  info->N = P.N;
+  info->l_max = P.p;
+  info->s = P.s;
+  info->m = P.m;
+  info->cost = P.cost;
+  info->actions = (P.p == 0) ? 1 : P.m + P.s * P.p + 1;
+  info->alpha = P.alpha;
+  info->log10_bound = P.log10_bound;
+  info->precision = P.opts.precision;
+  info->quad = P.opts.quad;
+  info->selector_used = P.opts.selector;
+  info->unique_factors = P.nuniq;
+  info->device_bytes = P.device_bytes;
+  return PHIKRON_OK;
+}
+
+int phikron_plan_nodes(phikron_plan_t plan, double* x, double* w) {
+  clear_error();
+  if (!plan || !x || !w) { set_error("phikron_plan_nodes: NULL argument"); return PHIKRON_EINVAL; }
+  const Plan& P = plan->impl;
+  for (int k = 0; k < P.m; ++k) {
+    x[k] = P.x[k];
+    w[k] = P.w[k];
+  }
+  return PHIKRON_OK;
+}
+
+void phikron_destroy(phikron_plan_t plan) { delete plan; }
+
+int phikron_profile_begin(phikron_plan_t plan, int max_timed) {
+  clear_error();
+  if (!plan || max_timed < 0) { set_error("phikron_profile_begin: bad arguments"); return PHIKRON_EINVAL; }
+  Profiler& pr = plan->impl.prof;
+  DeviceGuard dg(plan->impl.opts.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  pr.launches = 0;
+  for (int c = 0; c < KC_COUNT; ++c) pr.launches_by_class[c] = 0;
+  pr.used = 0;
+  while ((int)pr.cls.size() < max_timed) {
+    cudaEvent_t a, b;
+    PK_TRY_CUDA(cudaEventCreate(&a));
+    PK_TRY_CUDA(cudaEventCreate(&b));
+    pr.ev.push_back(a);
+    pr.ev.push_back(b);
+    pr.cls.push_back(0);
+  }
+  pr.timing = max_timed > 0;
+  return PHIKRON_OK;
+}
+
+int phikron_profile_end(phikron_plan_t plan, phikron_profile* out) {
+  clear_error();
+  if (!plan || !out) { set_error("phikron_profile_end: NULL argument"); return PHIKRON_EINVAL; }
+  Profiler& pr = plan->impl.prof;
+  DeviceGuard dg(plan->impl.opts.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  std::memset(out, 0, sizeof(*out));
+  for (int c = 0; c < KC_COUNT; ++c) out->launches[c] = pr.launches_by_class[c];
+  for (size_t i = 0; i < pr.used; ++i) {
+    PK_TRY_CUDA(cudaEventSynchronize(pr.ev[2 * i + 1]));
+    float ms = 0.f;
+    PK_TRY_CUDA(cudaEventElapsedTime(&ms, pr.ev[2 * i], pr.ev[2 * i + 1]));
+    out->ms[pr.cls[i]] += ms;
+  }
+  out->timed_launches = (long long)pr.used;
+  pr.timing = false;
+  pr.used = 0;
+  return PHIKRON_OK;
+}
+
+int phikron_log_quaderr(double n, int p, double alpha, double beta, int rule, double* log_err) {
+  clear_error();
+  if (!log_err) { set_error("phikron_log_quaderr: NULL output"); return PHIKRON_EINVAL; }
+  return planner::log_quaderr(n, p, alpha, beta, rule, log_err);
+}
+
+int phikron_quadnodes(double eps, int p, double alpha, double beta, int rule, int* n) {
+  clear_error();
+  if (!n) { set_error("phikron_quadnodes: NULL output"); return PHIKRON_EINVAL; }
+  return planner::quadnodes(eps, p, alpha, beta, rule, n);
+}
+
+int phikron_setup_quadrature(double eps, int p, double alpha, double beta, int rule, int* s, int* m,
+                             int* cost) {
+  clear_error();
+  if (!s || !m || !cost) { set_error("phikron_setup_quadrature: NULL output"); return PHIKRON_EINVAL; }
+  return planner::setup_quadrature(eps, p, alpha, beta, rule, s, m, cost);
+}
+
+int phikron_gauss_legendre(int m, double* x, double* w) {
+  clear_error();
+  return planner::gauss_legendre(m, x, w);
+}
+
+int phikron_clenshaw_curtis(int n, double* x, double* w) {
+  clear_error();
+  return planner::clenshaw_curtis(n, x, w);
+}
+
+size_t phikron_expm_workspace_bytes(int count, int n) { return expm_workspace_bytes(count, n); }
+
+int phikron_expm_batched(int count, int n, const double* A, const double* scale,
+                         const double* norms1, double* E, void* workspace, void* stream) {
+  clear_error();
+  return expm_batched(count, n, A, scale, norms1, E, workspace, static_cast<cudaStream_t>(stream));
+}
+
+int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const double* V,
+                           double* Out, double* work, void* stream) {
+  clear_error();
+  if ((dims != 2 && dims != 3) || !n || !E || !V || !Out || !work) {
+    set_error("phikron_kron_apply_f64: bad arguments");
+    return PHIKRON_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double* cur = V;
+  for (int d = 0; d < dims; ++d) {
+    long long B0 = 1, R = 1;
+    for (int q = 0; q < d; ++q) B0 *= n[q];
+    for (int q = d + 1; q < dims; ++q) R *= n[q];
+    // ping-pong so that the last mode lands in Out: dims odd -> Out, work, Out ; even -> work, Out
+    double* dst = (((dims - 1 - d) % 2) == 0) ? Out : work;
+    PK_RET(mode_product_f64(cur, 0, dst, 0, E[d], 0, 1, B0, n[d], R, st));
+    cur = dst;
+  }
+  return PHIKRON_OK;
+}
+
+}  // extern "C"

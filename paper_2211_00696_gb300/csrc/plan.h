@@ -1,0 +1,62 @@
+// The plan object behind phikron_plan_t: everything Algorithm 6 computes before it sees v.
+#pragma once
+
+#include <vector>
+
+#include "common.h"
+#include "profile.h"
+
+namespace phikron {
+
+struct Plan {
+  int dims = 0;
+  int n[3] = {1, 1, 1};
+  long long N = 0;
+  double tau = 0.0;
+  int p = 0;            // l_max: orders 0..p are returned
+  double tol = 0.0;
+  phikron_opts opts{};
+  int s = 0, m = 0, cost = 0;
+  double alpha = 0.0, log10_bound = 0.0;
+  std::vector<double> x, w, coef;   // nodes, weights on [0,1]; coef[(j-1)*m + k]
+
+  // unique factors: uniq_of[d] -> u, uniq_rep[u] -> first d
+  int nuniq = 0;
+  int uniq_of[3] = {0, 0, 0};
+  int uniq_rep[3] = {0, 0, 0};
+  // per unique factor, nexp = m + 1 + s float64 matrices n_d x n_d:
+  //   [0, m)       E_k = exp((1 - x_k) 2^{-s} M^d)
+  //   m            exp(M^d)                      (phi_0)
+  //   m + 1 + t    G_t = exp(2^{t-s} M^d), t < s (squaring steps)
+  int nexp = 0;
+  double* dExp[3] = {nullptr, nullptr, nullptr};
+  double* dCoef = nullptr;
+
+  // float64 apply work buffers
+  double* dW1 = nullptr;
+  double* dW2 = nullptr;
+  double* dY = nullptr;
+  double* dYn = nullptr;
+  double* dV = nullptr;      // staging for phikron_apply_host
+  double* dOut = nullptr;
+
+  // mixed-precision state (owned by the precision back-end; see precision_setup)
+  void* mixed = nullptr;
+  void (*mixed_free)(void*) = nullptr;
+
+  Profiler prof;
+
+  size_t device_bytes = 0;
+  std::vector<void*> allocations;
+
+  int alloc(void** p, size_t bytes);
+  ~Plan();
+};
+
+int apply_f64(Plan& P, const double* V, double* Out, cudaStream_t st);
+// Prepares precision-specific plan state (no-op for FP64).
+int precision_setup(Plan& P);
+// Runs the apply for nrhs right-hand sides with the plan's precision.
+int apply_dispatch(Plan& P, int nrhs, const double* V, double* Out, cudaStream_t st);
+
+}  // namespace phikron

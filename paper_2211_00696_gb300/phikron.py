@@ -1,0 +1,271 @@
+"""Thin ctypes binding of libphikron (the C ABI in include/phikron.h).
+
+Argument marshalling only: every step of phi_l(-tau*A)v runs inside the CUDA library.
+Device buffers are torch CUDA tensors (PyTorch supplies device memory and streams); the
+library receives their raw pointers.  If the shared library is missing or cannot be
+loaded this module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libphikron.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONVERGED, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+QUAD_GAUSS, QUAD_CC = 0, 1
+PREC_FP64, PREC_TF32X3, PREC_OZAKI_BF16 = 0, 1, 2
+SELECT_PAPER, SELECT_MLP = 0, 1
+
+_ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
+             ENOTCONVERGED: "ENOTCONVERGED", ENOTSUP: "ENOTSUP"}
+
+
+class PhikronError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"phikron {_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("quad", C.c_int), ("precision", C.c_int), ("selector", C.c_int),
+                ("force_s", C.c_int), ("force_m", C.c_int), ("alpha", C.c_double),
+                ("beta", C.c_double), ("device", C.c_int), ("max_rhs", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("dims", C.c_int), ("n", C.c_int * 3), ("N", C.c_int64), ("l_max", C.c_int),
+                ("s", C.c_int), ("m", C.c_int), ("cost", C.c_int), ("actions", C.c_int),
+                ("alpha", C.c_double), ("log10_bound", C.c_double), ("precision", C.c_int),
+                ("quad", C.c_int), ("selector_used", C.c_int), ("unique_factors", C.c_int),
+                ("device_bytes", C.c_size_t)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 6), ("launches", C.c_longlong * 6), ("timed_launches", C.c_longlong)]
+
+
+KERNEL_CLASSES = ("gemm_f64", "weighted_sum", "squaring", "tc_mode", "convert", "other")
+
+_lib = None
+
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int)
+
+# name -> (restype, argtypes); every symbol declared in include/phikron.h
+SIGNATURES = {
+    "phikron_opts_default": (None, [C.POINTER(Opts)]),
+    "phikron_plan": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(_DP), _IP, C.c_double,
+                               C.c_int, C.c_double, C.POINTER(Opts)]),
+    "phikron_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phikron_apply_many": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phikron_apply_host": (C.c_int, [C.c_void_p, _DP, _DP, C.c_void_p]),
+    "phikron_plan_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    "phikron_plan_nodes": (C.c_int, [C.c_void_p, _DP, _DP]),
+    "phikron_destroy": (None, [C.c_void_p]),
+    "phikron_last_error": (C.c_char_p, []),
+    "phikron_profile_begin": (C.c_int, [C.c_void_p, C.c_int]),
+    "phikron_profile_end": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
+    "phikron_log_quaderr": (C.c_int, [C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _DP]),
+    "phikron_quadnodes": (C.c_int, [C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _IP]),
+    "phikron_setup_quadrature": (C.c_int, [C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
+                                           _IP, _IP, _IP]),
+    "phikron_gauss_legendre": (C.c_int, [C.c_int, _DP, _DP]),
+    "phikron_clenshaw_curtis": (C.c_int, [C.c_int, _DP, _DP]),
+    "phikron_expm_workspace_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "phikron_expm_batched": (C.c_int, [C.c_int, C.c_int, C.c_void_p, _DP, _DP, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]),
+    "phikron_kron_apply_f64": (C.c_int, [C.c_int, _IP, C.POINTER(C.c_void_p), C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]),
+}
+
+
+def lib():
+    """Loads libphikron.so (raises if it is absent: build it with paper_2211_00696_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libphikron.so not built at {LIB_PATH}; run "
+                              "`python -m paper_2211_00696_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise PhikronError(rc, lib().phikron_last_error().decode())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------------------- planner (host)
+
+def log_quaderr(n: float, p: int, alpha: float, beta: float = 1.0, rule: int = QUAD_GAUSS) -> float:
+    out = C.c_double()
+    _check(lib().phikron_log_quaderr(n, p, alpha, beta, rule, C.byref(out)))
+    return out.value
+
+
+def quadnodes(eps: float, p: int, alpha: float, beta: float = 1.0, rule: int = QUAD_GAUSS) -> int:
+    out = C.c_int()
+    _check(lib().phikron_quadnodes(eps, p, alpha, beta, rule, C.byref(out)))
+    return out.value
+
+
+def setup_quadrature(eps: float, p: int, alpha: float, beta: float = 1.0, rule: int = QUAD_GAUSS):
+    s, m, c = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().phikron_setup_quadrature(eps, p, alpha, beta, rule, C.byref(s), C.byref(m), C.byref(c)))
+    return s.value, m.value, c.value
+
+
+def gauss_legendre(m: int):
+    x, w = np.zeros(m), np.zeros(m)
+    _check(lib().phikron_gauss_legendre(m, _dp(x), _dp(w)))
+    return x, w
+
+
+def clenshaw_curtis(n: int):
+    x, w = np.zeros(n + 1), np.zeros(n + 1)
+    _check(lib().phikron_clenshaw_curtis(n, _dp(x), _dp(w)))
+    return x, w
+
+
+# ----------------------------------------------------------------------------- plans
+
+class Plan:
+    """phikron_plan_t owner.  ``factors``: list of 2 or 3 square float64 arrays (host)."""
+
+    def __init__(self, factors, tau: float, l_max: int, tol: float, *, precision: int = PREC_FP64,
+                 quad: int = QUAD_GAUSS, force_s: int = -1, force_m: int = -1, alpha: float = 0.0,
+                 beta: float = 0.0, device: int = -1, max_rhs: int = 1):
+        L = lib()
+        self._h = C.c_void_p()
+        facs = [np.ascontiguousarray(a, dtype=np.float64) for a in factors]
+        self._facs = facs
+        ptrs = (_DP * len(facs))(*[_dp(a) for a in facs])
+        ns = (C.c_int * len(facs))(*[a.shape[0] for a in facs])
+        for a in facs:
+            if a.ndim != 2 or a.shape[0] != a.shape[1]:
+                raise ValueError("factors must be square matrices")
+        o = Opts()
+        L.phikron_opts_default(C.byref(o))
+        o.quad, o.precision, o.force_s, o.force_m = quad, precision, force_s, force_m
+        o.alpha, o.beta, o.device, o.max_rhs = alpha, beta, device, max_rhs
+        _check(L.phikron_plan(C.byref(self._h), len(facs), ptrs, ns, tau, l_max, tol, C.byref(o)))
+        self.shape = tuple(a.shape[0] for a in facs)
+        self.N = int(np.prod(self.shape))
+        self.l_max = l_max
+        self.max_rhs = max_rhs
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(lib().phikron_plan_info(self._h, C.byref(inf)))
+        return {k: (list(getattr(inf, k)) if k == "n" else getattr(inf, k)) for k, _ in Info._fields_}
+
+    def nodes(self):
+        m = self.info()["m"]
+        x, w = np.zeros(max(m, 1)), np.zeros(max(m, 1))
+        _check(lib().phikron_plan_nodes(self._h, _dp(x), _dp(w)))
+        return x[:m], w[:m]
+
+    def apply(self, V, Out=None, stream=None):
+        """V: CUDA float64 tensor with N entries; returns Out of shape (l_max+1, N)."""
+        import torch
+        if V.dtype != torch.float64 or not V.is_cuda or not V.is_contiguous() or V.numel() != self.N:
+            raise ValueError("V must be a contiguous CUDA float64 tensor with N entries")
+        if Out is None:
+            Out = torch.empty((self.l_max + 1, self.N), dtype=torch.float64, device=V.device)
+        _check(lib().phikron_apply(self._h, V.data_ptr(), Out.data_ptr(), _stream_ptr(stream)))
+        return Out
+
+    def apply_many(self, V, Out=None, stream=None):
+        """V: (nrhs, N) CUDA float64; returns (nrhs, l_max+1, N)."""
+        import torch
+        nrhs = V.shape[0]
+        if Out is None:
+            Out = torch.empty((nrhs, self.l_max + 1, self.N), dtype=torch.float64, device=V.device)
+        _check(lib().phikron_apply_many(self._h, nrhs, V.data_ptr(), Out.data_ptr(), _stream_ptr(stream)))
+        return Out
+
+    def apply_host(self, v: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """Host-memory apply (copies in, applies, copies out; synchronous)."""
+        v = np.ascontiguousarray(v, dtype=np.float64).ravel()
+        if out is None:
+            out = np.empty((self.l_max + 1, self.N))
+        st = 0 if stream is None else _stream_ptr(stream)
+        _check(lib().phikron_apply_host(self._h, _dp(v), _dp(out), C.c_void_p(st)))
+        return out
+
+    def apply_host_ptr(self, v_ptr: int, out_ptr: int, stream=None):
+        """Host-memory apply on raw (e.g. pinned torch) host pointers."""
+        st = 0 if stream is None else _stream_ptr(stream)
+        _check(lib().phikron_apply_host(self._h, C.cast(C.c_void_p(v_ptr), _DP),
+                                        C.cast(C.c_void_p(out_ptr), _DP), C.c_void_p(st)))
+
+    def profile_begin(self, max_timed: int = 0):
+        """Count (and, if max_timed > 0, event-time) every kernel the applies launch."""
+        _check(lib().phikron_profile_begin(self._h, max_timed))
+
+    def profile_end(self) -> dict:
+        pr = Profile()
+        _check(lib().phikron_profile_end(self._h, C.byref(pr)))
+        return {"ms": dict(zip(KERNEL_CLASSES, list(pr.ms))),
+                "launches": dict(zip(KERNEL_CLASSES, list(pr.launches))),
+                "timed_launches": pr.timed_launches}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().phikron_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- kernels alone
+
+def expm_batched(A, scale, stream=None):
+    """E[b] = exp(scale[b] * A[b]); A: (count, n, n) CUDA float64 tensor; scale: host floats."""
+    import torch
+    count, n, _ = A.shape
+    A = A.contiguous()
+    sc = np.ascontiguousarray(scale, dtype=np.float64)
+    norms = np.ascontiguousarray(A.abs().sum(dim=1).max(dim=1).values.cpu().numpy(), dtype=np.float64)
+    E = torch.empty_like(A)
+    ws = torch.empty(int(lib().phikron_expm_workspace_bytes(count, n)) // 8 + 1, dtype=torch.float64,
+                     device=A.device)
+    _check(lib().phikron_expm_batched(count, n, A.data_ptr(), _dp(sc), _dp(norms), E.data_ptr(),
+                                      ws.data_ptr(), _stream_ptr(stream)))
+    return E
+
+
+def kron_apply_f64(mats, V, stream=None):
+    """(mats[0] (x) ... ) V for CUDA float64 tensors (mode products in float64)."""
+    import torch
+    ns = (C.c_int * len(mats))(*[m.shape[0] for m in mats])
+    ptrs = (C.c_void_p * len(mats))(*[m.contiguous().data_ptr() for m in mats])
+    out = torch.empty_like(V)
+    work = torch.empty_like(V)
+    _check(lib().phikron_kron_apply_f64(len(mats), ns, ptrs, V.data_ptr(), out.data_ptr(),
+                                        work.data_ptr(), _stream_ptr(stream)))
+    return out

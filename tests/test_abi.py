@@ -1,0 +1,90 @@
+"""The C-ABI library loads on a machine without a GPU, exports every symbol the header
+declares, and its host-only planner agrees exactly with the oracle planner."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2211_00696_gb300 as pk
+from paper_2211_00696_gb300 import phikron as B
+from oracle import planner as PL
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(phikron_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = pk.lib()
+    declared = _declared_functions()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared <= set(B.SIGNATURES), declared - set(B.SIGNATURES)
+
+
+def test_planner_matches_oracle_exactly():
+    for alpha in (0.37, 2.0, 8.712, 27.7092, 384.0, 1331.2, 85196.8, 3.1e5):
+        for tol in (1e-6, 1e-8, 1e-10, 1e-14):
+            for p in (1, 2, 3, 7, 20):
+                for rule, name in ((pk.QUAD_GAUSS, PL.GAUSS), (pk.QUAD_CC, PL.CC)):
+                    assert pk.setup_quadrature(tol, p, alpha, 1.0, rule) == tuple(
+                        PL.setup_quadrature(tol, p, alpha, 1.0, name)), (alpha, tol, p, rule)
+
+
+def test_log_quaderr_matches_oracle():
+    for n in (2, 3.5, 8, 17, 40):
+        for p in (1, 3, 20):
+            for alpha in (0.5, 5.0, 60.0):
+                a = pk.log_quaderr(n, p, alpha)
+                b = PL.log_quaderr(n, p, alpha, 1.0)
+                assert abs(a - b) <= 1e-9 * max(1.0, abs(b))
+
+
+def test_quadnodes_matches_oracle():
+    for eps in (1e-6, 1e-10, 1e-14):
+        for p in (1, 3, 20):
+            for alpha in (0.1, 3.0, 48.0):
+                assert pk.quadnodes(eps, p, alpha) == PL.quadnodes(eps, p, alpha, 1.0)
+
+
+def test_gauss_legendre_matches_library_rule():
+    for m in (1, 2, 3, 8, 9, 21, 37, 64):
+        x, w = pk.gauss_legendre(m)
+        xr, wr = PL.gauss_legendre_01(m)
+        assert np.max(np.abs(x - xr)) <= 2e-16 * 4
+        # numpy's leggauss weights drift ~1e-16*m^2 relative; the library's are pinned below
+        assert np.max(np.abs(w - wr)) <= 1e-12 * np.max(wr)
+        for k in range(2 * m):
+            assert abs(np.dot(w, x ** k) - 1.0 / (k + 1)) <= 2e-15
+
+
+def test_clenshaw_curtis_exact_on_polynomials():
+    for n in (2, 6, 12, 48):
+        x, w = pk.clenshaw_curtis(n)
+        for k in range(n + 1):
+            assert abs(np.dot(w, x ** k) - 1.0 / (k + 1)) <= 1e-14
+
+
+def test_invalid_arguments_return_einval_without_gpu():
+    with pytest.raises(pk.PhikronError) as e:
+        pk.gauss_legendre(0)
+    assert e.value.code == B.EINVAL
+    with pytest.raises(pk.PhikronError) as e:
+        pk.setup_quadrature(1e-10, 3, -1.0)
+    assert e.value.code == B.EINVAL
+    with pytest.raises(pk.PhikronError):
+        pk.Plan([np.eye(3), np.eye(3)], 0.1, 25, 1e-10)      # l_max > 20
+    with pytest.raises(pk.PhikronError):
+        pk.Plan([np.eye(3), np.full((3, 3), np.nan)], 0.1, 2, 1e-10)
+    with pytest.raises(pk.PhikronError):
+        pk.Plan([np.eye(3), np.eye(3)], 0.1, 2, 0.0)          # tol <= 0
