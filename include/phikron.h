@@ -47,11 +47,12 @@ extern "C" {
 #define PHIKRON_QUAD_CC           1   /* Clenshaw-Curtis nodes with the CC bound            */
 
 #define PHIKRON_PREC_FP64         0   /* every product in float64 (DFMA)                    */
-#define PHIKRON_PREC_TF32X3       1   /* mode products as 3 TF32 tensor-core passes (hi*hi +
-                                         hi*lo + lo*hi), FP32 accumulate; float64 expms,
-                                         weights and squaring recurrence                    */
-#define PHIKRON_PREC_OZAKI_BF16   2   /* mode products as exact BF16 slice products (Ozaki
-                                         splitting), combined in float64                    */
+#define PHIKRON_PREC_OZAKI_BF16   2   /* mixed: mode products on the tensor cores as exact
+                                         BF16 digit-slice products (Ozaki splitting, FP32
+                                         accumulation in TMEM); state, node weights and the
+                                         squaring recurrence in float-float (~48 bits);
+                                         1D exponentials in float64.  Needs every n[d] a
+                                         multiple of 16 in 16..128 and l_max <= 8.          */
 
 #define PHIKRON_SELECT_PAPER      0   /* (s, m) from Algorithm 5                            */
 #define PHIKRON_SELECT_MLP        1   /* (s, m) from the learned selector, Algorithm 5 as
@@ -68,6 +69,9 @@ typedef struct phikron_opts {
                          ||v||_inf)                                                         */
   int    device;      /* CUDA device ordinal; -1 = the calling thread's current device        */
   int    max_rhs;     /* largest nrhs passed to phikron_apply_many; default 1                 */
+  int    slices;      /* OZAKI_BF16: digit slices per operand, 3..6 (8 bits each; 3 ~ FP32,
+                         5 ~ 1e-12 per product); 0 = from tol (>=1e-5: 3, >=1e-7: 4,
+                         >=1e-10: 5, else 6)                                                */
 } phikron_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -137,6 +141,7 @@ typedef struct phikron_info {
   int    precision, quad, selector_used;
   int    unique_factors;
   size_t device_bytes; /* device memory held by the plan                                */
+  int    slices;       /* digit slices of the mixed path (0 for FP64)                   */
 } phikron_info;
 
 int  phikron_plan_info(phikron_plan_t plan, phikron_info* info);
@@ -145,6 +150,11 @@ int  phikron_plan_info(phikron_plan_t plan, phikron_info* info);
 int  phikron_plan_nodes(phikron_plan_t plan, double* x, double* w);
 
 void phikron_destroy(phikron_plan_t plan);
+
+/* Synchronises the device and reports whether a bounded device-side wait of an earlier
+ * apply on this plan expired (PHIKRON_ETIMEOUT; the status is then cleared).  The results
+ * of such an apply are undefined. */
+int phikron_check_status(phikron_plan_t plan);
 
 /* ------------------------------------------------------------------ per-kernel timing
  * Between phikron_profile_begin and phikron_profile_end every kernel the plan's applies

@@ -5,4 +5,4 @@ its Python binding (``phikron``) and build script (``build``).
 """
 from .phikron import (Plan, PhikronError, lib, log_quaderr, quadnodes, setup_quadrature,  # noqa: F401
                       gauss_legendre, clenshaw_curtis, expm_batched, kron_apply_f64,
-                      PREC_FP64, PREC_TF32X3, PREC_OZAKI_BF16, QUAD_GAUSS, QUAD_CC)
+                      PREC_FP64, PREC_OZAKI_BF16, QUAD_GAUSS, QUAD_CC)

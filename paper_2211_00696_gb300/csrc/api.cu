@@ -72,6 +72,7 @@ double norm_one(const double* a, int n) {
 
 Plan::~Plan() {
   for (void* p : allocations) cudaFree(p);
+  if (mixed && mixed_free) mixed_free(mixed);
 }
 
 int Plan::alloc(void** p, size_t bytes) {
@@ -317,6 +318,7 @@ void phikron_opts_default(phikron_opts* o) {
   o->beta = 0.0;
   o->device = -1;
   o->max_rhs = 1;
+  o->slices = 0;
 }
 
 const char* phikron_last_error(void) { return g_err.c_str(); }
@@ -344,7 +346,7 @@ int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const in
   phikron_opts_default(&o);
   if (opts) o = *opts;
   if (o.quad != PHIKRON_QUAD_GAUSS && o.quad != PHIKRON_QUAD_CC) { set_error("phikron_plan: bad quad"); return PHIKRON_EINVAL; }
-  if (o.precision < PHIKRON_PREC_FP64 || o.precision > PHIKRON_PREC_OZAKI_BF16) { set_error("phikron_plan: bad precision"); return PHIKRON_EINVAL; }
+  if (o.precision != PHIKRON_PREC_FP64 && o.precision != PHIKRON_PREC_OZAKI_BF16) { set_error("phikron_plan: bad precision"); return PHIKRON_EINVAL; }
   if (o.max_rhs < 1) o.max_rhs = 1;
   if (o.selector != PHIKRON_SELECT_PAPER) {
     set_error("phikron_plan: selector MLP needs phikron_plan_select (not in this entry point)");
@@ -422,6 +424,7 @@ int phikron_plan_info(phikron_plan_t plan, phikron_info* info) {
   info->selector_used = P.opts.selector;
   info->unique_factors = P.nuniq;
   info->device_bytes = P.device_bytes;
+  info->slices = P.mixed ? mixed_slices(P) : 0;
   return PHIKRON_OK;
 }
 
@@ -437,6 +440,21 @@ int phikron_plan_nodes(phikron_plan_t plan, double* x, double* w) {
 }
 
 void phikron_destroy(phikron_plan_t plan) { delete plan; }
+
+int phikron_check_status(phikron_plan_t plan) {
+  clear_error();
+  if (!plan) { set_error("phikron_check_status: NULL plan"); return PHIKRON_EINVAL; }
+  DeviceGuard dg(plan->impl.opts.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  PK_TRY_CUDA(cudaDeviceSynchronize());
+  int st = 0;
+  PK_RET(mixed_status(plan->impl, &st));
+  if (st != 0) {
+    set_error("a bounded device wait expired during an earlier apply");
+    return st;
+  }
+  return PHIKRON_OK;
+}
 
 int phikron_profile_begin(phikron_plan_t plan, int max_timed) {
   clear_error();

@@ -3,16 +3,13 @@
 
 namespace phikron {
 
-int precision_setup(Plan& P) {
-  if (P.opts.precision == PHIKRON_PREC_FP64) return PHIKRON_OK;
-  set_error("precision mode not built yet");
-  return PHIKRON_ENOTSUP;
-}
-
 int apply_dispatch(Plan& P, int nrhs, const double* V, double* Out, cudaStream_t st) {
   const long long N = P.N;
   for (int r = 0; r < nrhs; ++r) {
-    PK_RET(apply_f64(P, V + (size_t)r * N, Out + (size_t)r * (P.p + 1) * N, st));
+    if (P.opts.precision == PHIKRON_PREC_OZAKI_BF16)
+      PK_RET(apply_mixed(P, V + (size_t)r * N, Out + (size_t)r * (P.p + 1) * N, st));
+    else
+      PK_RET(apply_f64(P, V + (size_t)r * N, Out + (size_t)r * (P.p + 1) * N, st));
   }
   return PHIKRON_OK;
 }

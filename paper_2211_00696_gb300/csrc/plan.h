@@ -54,6 +54,10 @@ struct Plan {
 };
 
 int apply_f64(Plan& P, const double* V, double* Out, cudaStream_t st);
+int apply_mixed(Plan& P, const double* V, double* Out, cudaStream_t st);
+// Reads and clears the device status word of the mixed path (synchronous).
+int mixed_status(Plan& P, int* status);
+int mixed_slices(const Plan& P);
 // Prepares precision-specific plan state (no-op for FP64).
 int precision_setup(Plan& P);
 // Runs the apply for nrhs right-hand sides with the plan's precision.

@@ -1,0 +1,584 @@
+// K2 (mixed precision): mode products of Eq. (8) on the tcgen05 tensor cores with exact
+// BF16 slice products (Ozaki-style splitting), accumulated in TMEM.
+//
+// A mode product out[b][i0][i][r] = sum_k E[i][k] in[b][i0][k][r] is computed with both
+// operands cut into KS "digit" slices:
+//   in  ~ 2^{eX}   * sum_t x_t,  x_t = +-d_t 2^{-8t}, d_t in [0, 255]   (per-vector exponent eX;
+//        the digits are those of |in| * 2^{-eX} rounded to nearest at digit KS)
+//   E   ~ 2^{f_i}  * sum_s e_s,  e_s likewise                           (per-row exponent f_i)
+// Every slice value is exactly representable in BF16.  The slice pairs (s, t) with
+// s + t <= KS + 1 are multiplied on the tensor cores (kind::f16, BF16 inputs, FP32
+// accumulation): level 2 = (1,1) and level 3 = (1,2)+(2,1) sums are exact in FP32 (at most
+// 2 * 255^2 * 128 < 2^24), level 4 has its own accumulator (rounding 2^-24 of a
+// 2^-16-relative term) and levels >= 5 share a fourth (2^-24 of 2^-24).  Four accumulators
+// of 128 FP32 columns fill the 512 TMEM columns.  A single accumulator for levels >= 4
+// would take ~K/16 * (#pairs) FP32 roundings of a 2^-16-relative term per output and
+// leave a ~1e-10 floor.  The epilogue adds the accumulators in float-float (compensated
+// FP32) arithmetic and scales by 2^{eX + f_i}.  Result accuracy per product is
+// about 2^{1-8 KS} relative to ||E||_inf max|in|: KS = 3 ~ FP32, KS = 5 ~ 1e-12.
+//
+// No float64 arithmetic runs per element (GB300 executes float64 at ~1/64 of FP32): the
+// digits are cut from the float64 or float-float bit patterns with integer shifts, and the
+// state between passes is float-float (hi, lo) FP32 pairs.
+//
+// Two formulations share one kernel:
+//   TRANS (R > 1, contraction over a non-fastest axis):  D[r][i] = sum_k X^T[r][k] E[i][k]
+//       A = X^T tile (128 r-rows, K-major, transposed while slicing), B = E (n rows).
+//       TMEM lane = r, column = i; stores out[i][r] coalesced over lanes.
+//   NORMAL (R = 1, contraction over the fastest axis):   D[i][row] = sum_k E[i][k] X[row][k]
+//       A = E (128 rows, zero-padded), B = X tile (128 rows).  TMEM lane = i, column = row;
+//       stores out[row][i] coalesced over lanes.
+// K (= n) is processed in chunks of 32 through a 2-stage shared-memory ring: while the
+// tensor cores work on chunk c, 512 threads cut chunk c+1 (four threads per operand row,
+// 8 k each, with the raw values of the following chunk -- or of the next tile's first
+// chunk -- already in flight), and the E slices of the chunk arrive by one asynchronous
+// bulk copy (TMA) per chunk.  Operands use the
+// no-swizzle K-major canonical layout (8-row x 16-byte core matrices; LBO = 128 B between
+// core matrices along K, SBO = 512 B between 8-row groups).
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel records PHIKRON_ETIMEOUT in the
+// status word, waits (bounded) for its own tensor-core work, frees its TMEM and returns.
+#include <cstdint>
+
+#include "common.h"
+#include "mixed.h"
+#include "profile.h"
+
+namespace phikron {
+namespace tc {
+
+namespace {
+
+constexpr int KC = 32;                    // K elements per chunk
+constexpr int SLICE_BYTES = 128 * KC * 2; // one slice of a 128-row chunk: 8 KB
+constexpr int NTHREADS = 512;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on any single wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  // no swizzle, K-major: LBO = 128 B (next core matrix along K), SBO = 512 B (next 8 rows)
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for sm_100-class tensor cores
+  return d;
+}
+
+__device__ __forceinline__ uint32_t make_idesc(int M, int N) {
+  // kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1), both K-major,
+  // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait (wall clock); returns false on expiry
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  if (mbar_try(mbar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    if (mbar_try(mbar, parity)) return true;
+    if (global_ns() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------- digit cutting (integer ops)
+// F = |x| * 2^{64 - eX} as a 64-bit fixed-point integer (|x| < 2^eX); the digits d_t are the
+// bytes of F, most significant first.
+
+// m * 2^sh for a 24-bit m and sh <= 40 (bits below 2^0 are dropped)
+__device__ __forceinline__ uint64_t place24(uint32_t m, int sh) {
+  return sh >= 0 ? ((uint64_t)m << sh) : (uint64_t)(m >> min(-sh, 31));
+}
+
+// float64 input; eb = 1011 + eX
+__device__ __forceinline__ uint64_t fixed_f64(double x, int eb, uint32_t& sgn) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  sgn = (uint32_t)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull);
+  const int sh = ex - eb;  // <= 11
+  return sh >= 0 ? (m << sh) : (m >> min(-sh, 63));
+}
+
+// float-float input (hi, lo) with |lo| <= ulp(hi)/2; eb = 86 + eX
+__device__ __forceinline__ uint64_t fixed_ff(float hi, float lo, int eb, uint32_t& sgn) {
+  const uint32_t bh = __float_as_uint(hi), bl = __float_as_uint(lo);
+  sgn = bh & 0x80000000u;
+  const uint32_t eh = (bh >> 23) & 0xFFu, el = (bl >> 23) & 0xFFu;
+  const uint32_t mh = (bh & 0x7FFFFFu) | (eh ? 0x800000u : 0u);
+  const uint32_t ml = (bl & 0x7FFFFFu) | (el ? 0x800000u : 0u);
+  const uint64_t Fh = place24(mh, (int)eh - eb);
+  const uint64_t Fl = place24(ml, (int)el - eb);
+  return ((bh ^ bl) & 0x80000000u) ? Fh - Fl : Fh + Fl;
+}
+
+// round to nearest at digit KS, saturating on carry-out
+template <int KS>
+__device__ __forceinline__ uint64_t round_digits(uint64_t F) {
+  const uint64_t G = F + (1ull << (63 - 8 * KS));
+  return G < F ? ~0ull : G;
+}
+
+// The signed slice value +-d_t 2^{-8t} as an FP32 whose upper 16 bits are its (exact) BF16:
+// one byte permute puts d_t under the exponent of 2^23 (with the element's sign), one add
+// removes 2^23, one multiply applies 2^{-8t}.
+template <int T>
+__device__ __forceinline__ float digit_value(uint32_t w1, uint32_t w0, uint32_t magic, float unmagic) {
+  constexpr uint32_t byte = (T <= 4) ? (4 - T) : (8 - T);
+  const uint32_t w = (T <= 4) ? w1 : w0;
+  const float f = __uint_as_float(__byte_perm(w, magic, byte | 0x7540u)) + unmagic;
+  return f * __uint_as_float((uint32_t)(127 - 8 * T) << 23);
+}
+
+template <int KS, int T = 1>
+__device__ __forceinline__ void cut_pair(uint64_t F0, uint32_t s0, uint64_t F1, uint32_t s1, uint32_t* out) {
+  if constexpr (T <= KS) {
+    const float a = digit_value<T>((uint32_t)(F0 >> 32), (uint32_t)F0, 0x4B000000u | s0, s0 ? 8388608.0f : -8388608.0f);
+    const float b = digit_value<T>((uint32_t)(F1 >> 32), (uint32_t)F1, 0x4B000000u | s1, s1 ? 8388608.0f : -8388608.0f);
+    out[T - 1] = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632u);  // (bf16(b) << 16) | bf16(a)
+    cut_pair<KS, T + 1>(F0, s0, F1, s1, out);
+  }
+}
+
+// ---------------------------------------------------------------- float-float helpers
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+// float-float -> float64 by integer assembly of the 53-bit significand (no float64 ops);
+// requires |lo| <= ulp(hi)/2.
+__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
+  const uint32_t bh = __float_as_uint(hi);
+  const int eh = (int)((bh >> 23) & 0xFF);
+  if (eh == 0) return 0.0;
+  uint64_t M = (uint64_t)((bh & 0x7FFFFFu) | 0x800000u) << 29;
+  int E = eh - 127 + 1023;
+  const uint32_t bl = __float_as_uint(lo);
+  const int el = (int)((bl >> 23) & 0xFF);
+  if (el != 0) {
+    const uint64_t ml = (uint64_t)((bl & 0x7FFFFFu) | 0x800000u);
+    const int sh = el - eh + 29;
+    const uint64_t L = sh >= 0 ? (ml << sh) : (sh > -40 ? ((ml + (1ull << (-sh - 1))) >> (-sh)) : 0ull);
+    if (((bh ^ bl) >> 31) == 0) {
+      M += L;
+      if (M >> 53) { M >>= 1; ++E; }
+    } else {
+      M -= L;
+      while (M && !(M >> 52)) { M <<= 1; --E; }
+    }
+  }
+  return __longlong_as_double((long long)(((uint64_t)(bh >> 31) << 63) | ((uint64_t)E << 52) | (M & 0xFFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ float pow2f(int e) {
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return __uint_as_float((uint32_t)(e + 127) << 23);
+}
+
+
+}  // namespace
+
+// ---------------------------------------------------------------- the kernel
+
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Raw operand values of one thread for one chunk: 8 consecutive k of its operand row.
+template <bool IN_F64>
+struct Raw {
+  double d[IN_F64 ? 8 : 1];
+  float2 f[IN_F64 ? 1 : 8];
+};
+
+struct TileCtx {
+  int job;
+  long long b0, r0, row0;
+  int eX;
+  long long in_base, gr;
+  bool valid_row;
+};
+
+template <bool TRANS>
+__device__ __forceinline__ TileCtx tile_ctx(const ModePass& P, long long tile, long long tiles_per_job,
+                                            long long rtiles, int orow) {
+  TileCtx t;
+  t.job = (int)(tile / tiles_per_job);
+  const long long tj = tile % tiles_per_job;
+  t.b0 = t.r0 = t.row0 = 0;
+  if (TRANS) {
+    t.b0 = tj / rtiles;
+    t.r0 = (tj % rtiles) * 128;
+  } else {
+    t.row0 = tj * 128;
+  }
+  int eX = *P.jobs[t.job].in_exp;
+  t.eX = eX < -600 ? 0 : eX;  // all-zero input
+  t.in_base = TRANS ? t.b0 * (long long)P.n * P.R : 0;
+  t.gr = TRANS ? t.r0 + orow : t.row0 + orow;
+  t.valid_row = TRANS ? (t.gr < P.R) : (t.gr < P.B0);
+  return t;
+}
+
+template <bool IN_F64, bool TRANS>
+__device__ __forceinline__ void load_raw(const ModePass& P, const TileCtx& t, int c, int kq, Raw<IN_F64>& raw) {
+  const void* in = P.jobs[t.job].in;
+  const int n = P.n;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int k = c * KC + kq * 8 + e;
+    const bool ok = t.valid_row && k < n;
+    const long long idx = TRANS ? t.in_base + (long long)k * P.R + t.gr : t.gr * (long long)n + k;
+    if (IN_F64)
+      raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(in) + idx) : 0.0;
+    else
+      raw.f[e] = ok ? __ldg(reinterpret_cast<const float2*>(in) + idx) : make_float2(0.f, 0.f);
+  }
+}
+
+template <int KS, bool IN_F64, bool TRANS>
+__global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant__ ModePass P, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  // [stage 0: X slices KS*8K | E slices KS*8K][stage 1: ...][mbarriers][column scales][tmem]
+  constexpr int STAGE_BYTES = 2 * KS * SLICE_BYTES;
+  uint64_t* mbar_mma = reinterpret_cast<uint64_t*>(smem + 2 * STAGE_BYTES);   // 2: MMAs of stage done
+  uint64_t* mbar_e = mbar_mma + 2;                                             // 2: E slices of stage landed
+  float* scale_s = reinterpret_cast<float*>(smem + 2 * STAGE_BYTES + 64);     // 128 floats: 2^{eX + f_i}
+  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(smem + 2 * STAGE_BYTES + 64 + 512);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int orow = tid & 127;   // operand row owned by this thread (r for TRANS, row for NORMAL)
+  const int kq = tid >> 7;      // which 8 of the chunk's 32 k this thread cuts
+  const int n = P.n;
+  const int nchunks = (n + KC - 1) / KC;
+  const long long R = P.R, B0 = P.B0;
+  const long long rtiles = TRANS ? (R + 127) / 128 : 1;
+  const long long tiles_per_job = TRANS ? B0 * rtiles : (B0 + 127) / 128;
+  const long long total_tiles = tiles_per_job * P.njobs;
+
+  if (tid == 0) {
+    for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_mma[q])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_s)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_s;
+  const uint32_t idesc = TRANS ? make_idesc(128, n) : make_idesc(128, 128);
+
+  uint32_t it = 0;          // global chunk counter (stage = it & 1, use = it >> 1)
+  bool aborted = false;
+  int fail = 0;             // thread 0: an E-slice wait expired
+
+  long long tile = blockIdx.x;
+  TileCtx T;
+  Raw<IN_F64> raw;
+  if (tile < total_tiles) {
+    T = tile_ctx<TRANS>(P, tile, tiles_per_job, rtiles, orow);
+    load_raw<IN_F64, TRANS>(P, T, 0, kq, raw);
+  }
+  for (; tile < total_tiles && !aborted; tile += gridDim.x) {
+    const ModeJob& J = P.jobs[T.job];
+    if (tid < 128) {
+      const int E = T.eX + ((tid < n) ? J.rexp[tid] : 0);
+      scale_s[tid] = pow2f(E);
+    }
+    const int eb = IN_F64 ? 1011 + T.eX : 86 + T.eX;
+    bool init[4] = {false, false, false, false};
+    TileCtx Tn = T;
+    const long long next_tile = tile + gridDim.x;
+    for (int c = 0; c < nchunks; ++c, ++it) {
+      const uint32_t st = it & 1u;
+      uint8_t* sX = smem + st * STAGE_BYTES;
+      uint8_t* sE = sX + KS * SLICE_BYTES;
+      int timed_out = fail;
+      if (it >= 2) timed_out |= mbar_wait(smem_u32(&mbar_mma[st]), ((it >> 1) - 1) & 1u) ? 0 : 1;
+      if (__syncthreads_or(timed_out)) {  // block-uniform decision
+        aborted = true;
+        break;
+      }
+      if (tid == 0) {  // E slices of chunk c: one asynchronous bulk copy
+        const uint32_t bytes = (uint32_t)(KS * SLICE_BYTES);
+        mbar_expect_tx(smem_u32(&mbar_e[st]), bytes);
+        bulk_copy_g2s(smem_u32(sE), J.eslices + (size_t)c * KS * SLICE_BYTES, bytes, smem_u32(&mbar_e[st]));
+      }
+      // raw values of the next chunk (or of the next tile's first chunk) go in flight now
+      Raw<IN_F64> rawn;
+      if (c + 1 < nchunks) {
+        load_raw<IN_F64, TRANS>(P, T, c + 1, kq, rawn);
+      } else if (next_tile < total_tiles) {
+        Tn = tile_ctx<TRANS>(P, next_tile, tiles_per_job, rtiles, orow);
+        load_raw<IN_F64, TRANS>(P, Tn, 0, kq, rawn);
+      }
+      uint32_t pk[KS][4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        uint32_t s0, s1;
+        uint64_t F0, F1;
+        if (IN_F64) {
+          F0 = fixed_f64(raw.d[e], eb, s0);
+          F1 = fixed_f64(raw.d[e + 1], eb, s1);
+        } else {
+          F0 = fixed_ff(raw.f[e].x, raw.f[e].y, eb, s0);
+          F1 = fixed_ff(raw.f[e + 1].x, raw.f[e + 1].y, eb, s1);
+        }
+        F0 = round_digits<KS>(F0);
+        F1 = round_digits<KS>(F1);
+        uint32_t w[KS];
+        cut_pair<KS>(F0, s0, F1, s1, w);
+#pragma unroll
+        for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
+      }
+      {
+        const uint32_t off = (uint32_t)(orow >> 3) * 512u + (uint32_t)kq * 128u + (uint32_t)(orow & 7) * 16u;
+#pragma unroll
+        for (int sl = 0; sl < KS; ++sl)
+          *reinterpret_cast<uint4*>(sX + sl * SLICE_BYTES + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        if (!mbar_wait(smem_u32(&mbar_e[st]), (it >> 1) & 1u)) {
+          fail = 1;  // E never landed: skip the MMAs; the next vote aborts the block
+        } else {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t xa = smem_u32(sX), ea = smem_u32(sE);
+#pragma unroll
+          for (int s = 1; s <= KS; ++s) {          // E slice
+#pragma unroll
+            for (int t = 1; t <= KS; ++t) {        // X slice
+              if (s + t > KS + 1) continue;
+              const int L = s + t - 2;
+              const int a = L < 3 ? L : 3;
+              const uint32_t dacc = tmem + (uint32_t)(a * 128);
+#pragma unroll
+              for (int ks = 0; ks < KC / 16; ++ks) {
+                const uint32_t xs = xa + (uint32_t)((t - 1) * SLICE_BYTES + ks * 256);
+                const uint32_t es = ea + (uint32_t)((s - 1) * SLICE_BYTES + ks * 256);
+                const uint64_t xd = make_desc(xs), ed = make_desc(es);
+                if (TRANS)
+                  mma_bf16(dacc, xd, ed, idesc, init[a] ? 1u : 0u);
+                else
+                  mma_bf16(dacc, ed, xd, idesc, init[a] ? 1u : 0u);
+                init[a] = true;
+              }
+            }
+          }
+          mma_commit(smem_u32(&mbar_mma[st]));
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) init[a] = true;
+      raw = rawn;
+    }
+    if (aborted) break;
+    // epilogue: wait for the last chunk's MMAs (covers every earlier MMA of this tile)
+    {
+      const uint32_t lastit = it - 1;
+      int to = fail;
+      to |= mbar_wait(smem_u32(&mbar_mma[lastit & 1u]), (lastit >> 1) & 1u) ? 0 : 1;
+      if (__syncthreads_or(to)) aborted = true;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!aborted) {
+      // warps w, w+4, w+8, w+12 share TMEM lanes 32*(w%4)..+31 and split the columns
+      const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+      const int lrow = (warp & 3) * 32 + lane;  // TMEM lane of this thread
+      const int cq = warp >> 2;
+      int emax = -1000;
+      const int ncols = TRANS ? ((n + 15) & ~15) : 128;
+      const int ngroups = ncols / 16;
+      const int gbeg = (cq * ngroups) / 4, gend = ((cq + 1) * ngroups) / 4;
+      float2* outFF = reinterpret_cast<float2*>(J.out);
+      double* outF64 = reinterpret_cast<double*>(J.out);
+      const long long out_base = TRANS ? T.b0 * (long long)n * R : 0;
+      const float lane_scale = TRANS ? 1.0f : scale_s[lrow];
+      for (int gq = gbeg; gq < gend; ++gq) {
+        const int cc = gq * 16;
+        float d2[16], d3[16], d4[16], d5[16];
+        tmem_ld16(lane_base + (uint32_t)cc, d2);
+        tmem_ld16(lane_base + 128u + (uint32_t)cc, d3);
+        tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
+        tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = cc + j;
+          int i;
+          long long oidx;
+          bool ok;
+          float sc;
+          if (TRANS) {
+            i = col;
+            const long long g = T.r0 + lrow;
+            ok = (i < n) && (g < R);
+            oidx = out_base + (long long)i * R + g;
+            sc = scale_s[i];
+          } else {
+            i = lrow;
+            const long long g = T.row0 + col;
+            ok = (i < n) && (g < B0);
+            oidx = g * (long long)n + i;
+            sc = lane_scale;
+          }
+          if (!ok) continue;
+          // full two-sums at every step: D4 + D5 spans ~31 bits for 6 digits (a plain FP32
+          // add would round at 2^-42 of D2), and an element whose leading digit is small has
+          // |D2| < |D3 + ...|, where a fast two-sum would lose the error term
+          float t45, e45, u, eu, hi, eh;
+          two_sum(d4[j], d5[j], t45, e45);
+          two_sum(d3[j], t45, u, eu);
+          two_sum(d2[j], u, hi, eh);
+          float lo = eh + (eu + e45);
+          fast_two_sum(hi, lo, hi, lo);
+          hi *= sc;
+          lo *= sc;
+          if (J.out_f64)
+            outF64[oidx] = ff_to_f64(hi, lo);
+          else
+            outFF[oidx] = make_float2(hi, lo);
+          emax = max(emax, (int)((__float_as_uint(hi) >> 23) & 0xFFu));
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      // |v| < 2^{biased - 126}; a zero vector keeps the slot's initial (very negative) value
+      if (lane == 0 && J.out_exp && emax > 0) atomicMax(J.out_exp, emax - 126);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    T = Tn;
+  }
+  if (aborted && tid == 0) {
+    atomicExch(status, PHIKRON_ETIMEOUT);
+    // give in-flight tensor-core work and copies a bounded chance to drain before TMEM is freed
+    const uint32_t lastit = it > 0 ? it - 1 : 0;
+    mbar_wait(smem_u32(&mbar_mma[lastit & 1u]), (lastit >> 1) & 1u);
+    mbar_wait(smem_u32(&mbar_e[lastit & 1u]), (lastit >> 1) & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+template <int KS>
+size_t smem_bytes() {
+  return (size_t)2 * 2 * KS * SLICE_BYTES + 64 + 512 + 16 + 16;
+}
+
+template <int KS, bool IN_F64, bool TRANS>
+int launch_one(const ModePass& P, int* status, int nsm, cudaStream_t st) {
+  const size_t sm = smem_bytes<KS>();
+  auto kern = mode_kernel<KS, IN_F64, TRANS>;
+  static bool attr = false;  // per instantiation
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) {
+      set_error(std::string("tc mode kernel smem attribute: ") + cudaGetErrorString(e));
+      return PHIKRON_ECUDA;
+    }
+    attr = true;
+  }
+  const long long rtiles = TRANS ? (P.R + 127) / 128 : 1;
+  const long long tiles = (TRANS ? P.B0 * rtiles : (P.B0 + 127) / 128) * P.njobs;
+  const int grid = (int)(tiles < nsm ? tiles : nsm);
+  if (grid <= 0) return PHIKRON_OK;
+  launch_begin(KC_TC_MODE, st);
+  kern<<<grid, NTHREADS, sm, st>>>(P, status);
+  launch_end(st);
+  PK_CHECK_LAUNCH();
+  return PHIKRON_OK;
+}
+
+template <int KS>
+int launch_ks(const ModePass& P, int* status, int nsm, cudaStream_t st) {
+  const bool trans = P.R > 1;
+  if (P.in_f64) {
+    return trans ? launch_one<KS, true, true>(P, status, nsm, st) : launch_one<KS, true, false>(P, status, nsm, st);
+  }
+  return trans ? launch_one<KS, false, true>(P, status, nsm, st) : launch_one<KS, false, false>(P, status, nsm, st);
+}
+
+int mode_pass(const ModePass& P, int ks, int* status, int nsm, cudaStream_t st) {
+  if (P.njobs <= 0) return PHIKRON_OK;
+  if (P.n < 16 || P.n > 128 || (P.n % 16) != 0) {
+    set_error("tc mode pass: n must be a multiple of 16 in 16..128");
+    return PHIKRON_ENOTSUP;
+  }
+  switch (ks) {
+    case 3: return launch_ks<3>(P, status, nsm, st);
+    case 4: return launch_ks<4>(P, status, nsm, st);
+    case 5: return launch_ks<5>(P, status, nsm, st);
+    case 6: return launch_ks<6>(P, status, nsm, st);
+    default:
+      set_error("tc mode pass: slices must be 3..6");
+      return PHIKRON_EINVAL;
+  }
+}
+
+}  // namespace tc
+}  // namespace phikron

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libphikron.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONVERGED, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 QUAD_GAUSS, QUAD_CC = 0, 1
-PREC_FP64, PREC_TF32X3, PREC_OZAKI_BF16 = 0, 1, 2
+PREC_FP64, PREC_OZAKI_BF16 = 0, 2
 SELECT_PAPER, SELECT_MLP = 0, 1
 
 _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
@@ -33,7 +33,7 @@ class PhikronError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("quad", C.c_int), ("precision", C.c_int), ("selector", C.c_int),
                 ("force_s", C.c_int), ("force_m", C.c_int), ("alpha", C.c_double),
-                ("beta", C.c_double), ("device", C.c_int), ("max_rhs", C.c_int)]
+                ("beta", C.c_double), ("device", C.c_int), ("max_rhs", C.c_int), ("slices", C.c_int)]
 
 
 class Info(C.Structure):
@@ -41,7 +41,7 @@ class Info(C.Structure):
                 ("s", C.c_int), ("m", C.c_int), ("cost", C.c_int), ("actions", C.c_int),
                 ("alpha", C.c_double), ("log10_bound", C.c_double), ("precision", C.c_int),
                 ("quad", C.c_int), ("selector_used", C.c_int), ("unique_factors", C.c_int),
-                ("device_bytes", C.c_size_t)]
+                ("device_bytes", C.c_size_t), ("slices", C.c_int)]
 
 
 class Profile(C.Structure):
@@ -66,6 +66,7 @@ SIGNATURES = {
     "phikron_plan_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "phikron_plan_nodes": (C.c_int, [C.c_void_p, _DP, _DP]),
     "phikron_destroy": (None, [C.c_void_p]),
+    "phikron_check_status": (C.c_int, [C.c_void_p]),
     "phikron_last_error": (C.c_char_p, []),
     "phikron_profile_begin": (C.c_int, [C.c_void_p, C.c_int]),
     "phikron_profile_end": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
@@ -154,7 +155,7 @@ class Plan:
 
     def __init__(self, factors, tau: float, l_max: int, tol: float, *, precision: int = PREC_FP64,
                  quad: int = QUAD_GAUSS, force_s: int = -1, force_m: int = -1, alpha: float = 0.0,
-                 beta: float = 0.0, device: int = -1, max_rhs: int = 1):
+                 beta: float = 0.0, device: int = -1, max_rhs: int = 1, slices: int = 0):
         L = lib()
         self._h = C.c_void_p()
         facs = [np.ascontiguousarray(a, dtype=np.float64) for a in factors]
@@ -167,7 +168,7 @@ class Plan:
         o = Opts()
         L.phikron_opts_default(C.byref(o))
         o.quad, o.precision, o.force_s, o.force_m = quad, precision, force_s, force_m
-        o.alpha, o.beta, o.device, o.max_rhs = alpha, beta, device, max_rhs
+        o.alpha, o.beta, o.device, o.max_rhs, o.slices = alpha, beta, device, max_rhs, slices
         _check(L.phikron_plan(C.byref(self._h), len(facs), ptrs, ns, tau, l_max, tol, C.byref(o)))
         self.shape = tuple(a.shape[0] for a in facs)
         self.N = int(np.prod(self.shape))
@@ -218,6 +219,10 @@ class Plan:
         st = 0 if stream is None else _stream_ptr(stream)
         _check(lib().phikron_apply_host(self._h, C.cast(C.c_void_p(v_ptr), _DP),
                                         C.cast(C.c_void_p(out_ptr), _DP), C.c_void_p(st)))
+
+    def check_status(self):
+        """Raises PhikronError(ETIMEOUT) if a bounded device wait of an earlier apply expired."""
+        _check(lib().phikron_check_status(self._h))
 
     def profile_begin(self, max_timed: int = 0):
         """Count (and, if max_timed > 0, event-time) every kernel the applies launch."""
