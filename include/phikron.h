@@ -216,6 +216,19 @@ int phikron_expm_batched(int count, int n, const double* A, const double* scale,
 int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const double* V,
                            double* Out, double* work, void* stream);
 
+/* Allocation-free phikron_kron_apply_f64 (the paper has no counterpart: this serves callers
+ * that may not allocate device memory at call time, e.g. hosts that route all device
+ * memory through their own pool, or latency-critical loops where cudaMalloc's implicit
+ * synchronisation is unacceptable).  Same result as phikron_kron_apply_f64 without the
+ * `work` argument: the intermediate lives in a built-in device array of
+ * phikron_noalloc_max_elements() float64 (8 MiB, held by every GPU that loads the library
+ * until exit).  prod n[d] above that limit returns PHIKRON_EINVAL.  No cudaMalloc/cudaFree
+ * is called.  The first call on a device looks the array's address up (make it before any
+ * stream capture).  All calls share the array: calls that overlap on the GPU race. */
+long long phikron_noalloc_max_elements(void);
+int phikron_kron_apply_f64_noalloc(int dims, const int* n, const double* const* E, const double* V,
+                                   double* Out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,9 @@ SIGNATURES = {
                                        C.c_void_p, C.c_void_p]),
     "phikron_kron_apply_f64": (C.c_int, [C.c_int, _IP, C.POINTER(C.c_void_p), C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phikron_noalloc_max_elements": (C.c_longlong, []),
+    "phikron_kron_apply_f64_noalloc": (C.c_int, [C.c_int, _IP, C.POINTER(C.c_void_p), C.c_void_p,
+                                                 C.c_void_p, C.c_void_p]),
 }
 
 
