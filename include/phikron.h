@@ -52,7 +52,9 @@ extern "C" {
                                          accumulation in TMEM); state, node weights and the
                                          squaring recurrence in float-float (~48 bits);
                                          1D exponentials in float64.  Needs every n[d] a
-                                         multiple of 16 in 16..128 and l_max <= 8.          */
+                                         multiple of 16 in 16..256, l_max <= 8, m <= 64.
+                                         For n[d] > 128 the second digit level of that mode
+                                         rounds at ~2^-32 relative (FP32-class products).   */
 
 #define PHIKRON_SELECT_PAPER      0   /* (s, m) from Algorithm 5                            */
 #define PHIKRON_SELECT_MLP        1   /* (s, m) from the learned selector, Algorithm 5 as
@@ -72,6 +74,9 @@ typedef struct phikron_opts {
   int    slices;      /* OZAKI_BF16: digit slices per operand, 3..6 (8 bits each; 3 ~ FP32,
                          5 ~ 1e-12 per product); 0 = from tol (>=1e-5: 3, >=1e-7: 4,
                          >=1e-10: 5, else 6)                                                */
+  int    half_step;   /* OZAKI_BF16 and l_max >= 1: also return phi_l(-tau/2*A) v, l = 0..l_max
+                         (the state before the last squaring step of Eq. (29); s >= 1 is then
+                         enforced).  Out then holds 2*(l_max+1) vectors: tau first, tau/2 next. */
 } phikron_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -116,7 +121,8 @@ int phikron_apply(phikron_plan_t plan, const double* V, double* Out, void* strea
 /*
  * phikron_apply_many -- nrhs independent right-hand sides in one call.
  *   V   : DEVICE, nrhs*N float64 (right-hand side r at V + r*N).
- *   Out : DEVICE, nrhs*(l_max+1)*N float64 (rhs r, order l at Out + (r*(l_max+1)+l)*N).
+ *   Out : DEVICE, nrhs*(l_max+1)*N float64 (rhs r, order l at Out + (r*(l_max+1)+l)*N);
+ *         with half_step, 2*(l_max+1) vectors per rhs.
  *   1 <= nrhs <= opts.max_rhs given at plan time.
  */
 int phikron_apply_many(phikron_plan_t plan, int nrhs, const double* V, double* Out, void* stream);
@@ -155,6 +161,45 @@ void phikron_destroy(phikron_plan_t plan);
  * apply on this plan expired (PHIKRON_ETIMEOUT; the status is then cleared).  The results
  * of such an apply are undefined. */
 int phikron_check_status(phikron_plan_t plan);
+
+/* ------------------------------------------------------------------ batched apply
+ * Many plans (uneven sizes, different tau) x nrhs right-hand sides in one call: every stage
+ * of Algorithm 1 + Algorithm 6 for all of them is one grouped persistent tensor-core launch
+ * (all nodes x orders x right-hand sides x instances), and the whole apply is one CUDA graph.
+ * Every plan must use PHIKRON_PREC_OZAKI_BF16 with the same digit-slice count, the same dims
+ * and l_max, on one device; at most 64 plans.  The plans must outlive the batch.
+ *
+ * phikron_batch_create: allocates the batch's work buffers (device memory ~ 8 bytes x
+ *   nrhs x sum_i (2 (m_i+2) + 2 l_max) N_i).  half_step != 0 also returns phi_l at tau/2
+ *   (plans made with opts.half_step).  autotune != 0: the first apply times the candidate
+ *   launch shapes (K chunk 32/64, job order, grid) and keeps the fastest.
+ * phikron_batch_apply: V[i] (DEVICE) holds nrhs vectors of plan i (rhs r at V[i] + r*N_i);
+ *   Out[i] (DEVICE) receives, per rhs r, (l_max+1)*(half_step ? 2 : 1) vectors at
+ *   Out[i] + r*(l_max+1)*(half_step ? 2 : 1)*N_i.  Asynchronous on stream except the first
+ *   apply of an autotuned batch, which synchronises.
+ */
+typedef struct phikron_batch_s* phikron_batch_t;
+
+typedef struct phikron_batch_info {
+  int       units;        /* plans x nrhs                                                  */
+  int       launches;     /* kernel launches per apply (all inside one graph)               */
+  long long mode_jobs;    /* (vector, matrix) mode products per apply                        */
+  int       graph;        /* 1 if the apply runs as a CUDA graph                             */
+  int       k_chunk;      /* chosen K chunk (32 or 64)                                       */
+  int       big_first;    /* 1 if jobs are ordered largest first                             */
+  int       grid;         /* CTAs per mode pass                                              */
+  int       candidates;   /* launch shapes considered                                       */
+  int       tuned;        /* 1 once the autotuner has run (or was not requested)             */
+  double    best_ms;      /* time of the chosen shape during tuning (0 if not tuned)          */
+  size_t    device_bytes; /* device memory held by the batch                                 */
+} phikron_batch_info;
+
+int  phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* plans, int nrhs,
+                          int half_step, int autotune);
+int  phikron_batch_apply(phikron_batch_t batch, const double* const* V, double* const* Out, void* stream);
+int  phikron_batch_get_info(phikron_batch_t batch, phikron_batch_info* info);
+int  phikron_batch_check_status(phikron_batch_t batch);
+void phikron_batch_destroy(phikron_batch_t batch);
 
 /* ------------------------------------------------------------------ per-kernel timing
  * Between phikron_profile_begin and phikron_profile_end every kernel the plan's applies

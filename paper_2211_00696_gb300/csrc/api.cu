@@ -127,6 +127,7 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
     }
     if (o.force_s >= 0) s = o.force_s;
     if (o.force_m >= 1) m = o.force_m;
+    if (o.half_step && s < 1) s = 1;  // the half-step state is the one before the last squaring
     if (o.quad == PHIKRON_QUAD_CC && m < 2) m = 2;
     if (m > 256 || s > 60) {
       set_error("plan: node count or scaling out of range (m <= 256, s <= 60)");
@@ -234,13 +235,13 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
 
   // apply work buffers
   const long long N = P.N;
-  const int nv = std::max(m + 1, std::max(l_max, 1));
+  const int nv = std::max(m + 2, std::max(l_max, 1));
   PK_RET(P.alloc((void**)&P.dW1, sizeof(double) * (size_t)nv * N));
   PK_RET(P.alloc((void**)&P.dW2, sizeof(double) * (size_t)nv * N));
   PK_RET(P.alloc((void**)&P.dY, sizeof(double) * (size_t)std::max(l_max, 1) * N));
   PK_RET(P.alloc((void**)&P.dYn, sizeof(double) * (size_t)std::max(l_max, 1) * N));
   PK_RET(P.alloc((void**)&P.dV, sizeof(double) * (size_t)N));
-  PK_RET(P.alloc((void**)&P.dOut, sizeof(double) * (size_t)(l_max + 1) * N));
+  PK_RET(P.alloc((void**)&P.dOut, sizeof(double) * (size_t)(l_max + 1) * (o.half_step ? 2 : 1) * N));
   PK_RET(precision_setup(P));
   return PHIKRON_OK;
 }
@@ -301,9 +302,6 @@ int apply_f64(Plan& P, const double* V, double* Out, cudaStream_t st) {
 // =============================================================================== C ABI
 using namespace phikron;
 
-struct phikron_plan_s {
-  Plan impl;
-};
 
 extern "C" {
 
@@ -319,6 +317,7 @@ void phikron_opts_default(phikron_opts* o) {
   o->device = -1;
   o->max_rhs = 1;
   o->slices = 0;
+  o->half_step = 0;
 }
 
 const char* phikron_last_error(void) { return g_err.c_str(); }
@@ -348,6 +347,14 @@ int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const in
   if (o.quad != PHIKRON_QUAD_GAUSS && o.quad != PHIKRON_QUAD_CC) { set_error("phikron_plan: bad quad"); return PHIKRON_EINVAL; }
   if (o.precision != PHIKRON_PREC_FP64 && o.precision != PHIKRON_PREC_OZAKI_BF16) { set_error("phikron_plan: bad precision"); return PHIKRON_EINVAL; }
   if (o.max_rhs < 1) o.max_rhs = 1;
+  if (o.half_step && o.precision != PHIKRON_PREC_OZAKI_BF16) {
+    set_error("phikron_plan: half_step outputs are built for the mixed path only");
+    return PHIKRON_ENOTSUP;
+  }
+  if (o.half_step && l_max == 0) {
+    set_error("phikron_plan: half_step needs l_max >= 1");
+    return PHIKRON_EINVAL;
+  }
   if (o.selector != PHIKRON_SELECT_PAPER) {
     set_error("phikron_plan: selector MLP needs phikron_plan_select (not in this entry point)");
     return PHIKRON_ENOTSUP;
@@ -399,7 +406,8 @@ int phikron_apply_host(phikron_plan_t plan, const double* V_host, double* Out_ho
     ProfScope ps(&P.prof);
     PK_RET(apply_dispatch(P, 1, P.dV, P.dOut, st));
   }
-  PK_TRY_CUDA(cudaMemcpyAsync(Out_host, P.dOut, sizeof(double) * P.N * (P.p + 1), cudaMemcpyDeviceToHost, st));
+  PK_TRY_CUDA(cudaMemcpyAsync(Out_host, P.dOut, sizeof(double) * P.N * (P.p + 1) * (P.opts.half_step ? 2 : 1),
+                              cudaMemcpyDeviceToHost, st));
   PK_TRY_CUDA(cudaStreamSynchronize(st));
   return PHIKRON_OK;
 }

@@ -17,6 +17,7 @@
 #include "mixed.h"
 #include "plan.h"
 #include "profile.h"
+#include "batch.h"
 
 namespace phikron {
 
@@ -102,64 +103,97 @@ __device__ __forceinline__ void warp_max_atomic(int v, int* slot) {
   if ((threadIdx.x & 31) == 0 && slot && v > -1000) atomicMax(slot, v);
 }
 
-constexpr int MAXP = 20;
-
-template <int P_, bool OUT_F64>
-__global__ void ff_weighted_sum_kernel(const float2* __restrict__ T, long long T_stride,
-                                       const float2* __restrict__ coef, int m, long long N,
-                                       void* __restrict__ Y, long long Y_stride, int* __restrict__ out_exp) {
-  extern __shared__ float2 cs[];  // P_ * m coefficients
-  for (int i = threadIdx.x; i < P_ * m; i += blockDim.x) cs[i] = coef[i];
-  __syncthreads();
-  int emax[P_];
-#pragma unroll
-  for (int j = 0; j < P_; ++j) emax[j] = -1000;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    float2 acc[P_];
-#pragma unroll
-    for (int j = 0; j < P_; ++j) acc[j] = make_float2(0.f, 0.f);
-    for (int k = 0; k < m; ++k) {
-      const float2 t = T[k * T_stride + i];
-#pragma unroll
-      for (int j = 0; j < P_; ++j) ff_fma(acc[j], cs[j * m + k], t);
-    }
-#pragma unroll
-    for (int j = 0; j < P_; ++j) {
-      if (OUT_F64)
-        reinterpret_cast<double*>(Y)[j * Y_stride + i] = ff_to_f64(acc[j].x, acc[j].y);
-      else
-        reinterpret_cast<float2*>(Y)[j * Y_stride + i] = acc[j];
-      if (acc[j].x != 0.f) emax[j] = max(emax[j], exp_plus1(acc[j].x));
-    }
-  }
-  if (!OUT_F64) {
-#pragma unroll
-    for (int j = 0; j < P_; ++j) warp_max_atomic(emax[j], out_exp ? out_exp + j : nullptr);
-  }
-}
+constexpr int MAXP = 8;
+constexpr int MAXM = 64;
+constexpr int EW_THREADS = 256;
+constexpr int EW_PER_THREAD = 4;
+constexpr long long EW_BLOCK = EW_THREADS * EW_PER_THREAD;
 
 struct InvFact {
   float2 f[MAXP + 1];  // 1/k! as float-float
 };
 
-template <int P_, bool OUT_F64>
-__global__ void ff_squaring_kernel(const float2* __restrict__ Z, const float2* __restrict__ Y,
-                                   void* __restrict__ Yn, long long N, long long stride,
-                                   int* __restrict__ out_exp, InvFact inv) {
+__device__ __forceinline__ int find_ejob(const EJob* jobs, int njobs, long long blk) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].block_begin <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void* tab_ptr(const void* const* tab, int e, long long off, void* direct) {
+  return e >= 0 ? (void*)((char*)tab[e] + off) : direct;
+}
+
+// y_j = sum_k coef[j][k] T_k in float-float (Algorithm 1, second step), grouped over jobs
+template <int P_>
+__global__ void __launch_bounds__(EW_THREADS) g_weighted_kernel(const EJob* __restrict__ jobs, int njobs,
+                                                                const void* const* ptrtab) {
+  __shared__ float2 cs[P_ * MAXM];
+  const int jb = find_ejob(jobs, njobs, blockIdx.x);
+  const EJob& J = jobs[jb];
+  const int m = J.m;
+  for (int i = threadIdx.x; i < P_ * m; i += EW_THREADS) cs[i] = J.coef[i];
+  __syncthreads();
+  void* out = tab_ptr(ptrtab, J.out_tab, J.tab_off_out, J.out);
+  void* out2 = tab_ptr(ptrtab, J.out2_tab, J.tab_off_out2, J.out2);
   int emax[P_];
 #pragma unroll
-  for (int j = 0; j < P_; ++j) emax[j] = -1000;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < N;
-       x += (long long)gridDim.x * blockDim.x) {
+  for (int j = 0; j < P_; ++j) emax[j] = 0;
+  const long long base = (blockIdx.x - J.block_begin) * EW_BLOCK;
+#pragma unroll
+  for (int e = 0; e < EW_PER_THREAD; ++e) {
+    const long long i = base + e * EW_THREADS + threadIdx.x;
+    if (i >= J.N) break;
+    float2 acc[P_];
+#pragma unroll
+    for (int j = 0; j < P_; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int k = 0; k < m; ++k) {
+      const float2 t = J.a[k * J.stride + i];
+#pragma unroll
+      for (int j = 0; j < P_; ++j) ff_fma(acc[j], cs[j * m + k], t);
+    }
+#pragma unroll
+    for (int j = 0; j < P_; ++j) {
+      if (J.out_f64)
+        reinterpret_cast<double*>(out)[j * J.stride + i] = ff_to_f64(acc[j].x, acc[j].y);
+      else
+        reinterpret_cast<float2*>(out)[j * J.stride + i] = acc[j];
+      if (out2) reinterpret_cast<double*>(out2)[j * J.stride + i] = ff_to_f64(acc[j].x, acc[j].y);
+      emax[j] = max(emax[j], (int)((__float_as_uint(acc[j].x) >> 23) & 0xFFu));
+    }
+  }
+  if (J.out_exp) {
+#pragma unroll
+    for (int j = 0; j < P_; ++j) warp_max_atomic(emax[j] > 0 ? emax[j] - 126 : -1000, J.out_exp + j);
+  }
+}
+
+// y-hat_i = 2^{-i}(Z_i + sum_{j<=i} y_j/(i-j)!), i = 1..p (Eq. (29)), grouped over jobs
+template <int P_>
+__global__ void __launch_bounds__(EW_THREADS) g_squaring_kernel(const EJob* __restrict__ jobs, int njobs,
+                                                                const void* const* ptrtab, InvFact inv) {
+  const int jb = find_ejob(jobs, njobs, blockIdx.x);
+  const EJob& J = jobs[jb];
+  void* out = tab_ptr(ptrtab, J.out_tab, J.tab_off_out, J.out);
+  void* out2 = tab_ptr(ptrtab, J.out2_tab, J.tab_off_out2, J.out2);
+  int emax[P_];
+#pragma unroll
+  for (int j = 0; j < P_; ++j) emax[j] = 0;
+  const long long base = (blockIdx.x - J.block_begin) * EW_BLOCK;
+#pragma unroll
+  for (int e = 0; e < EW_PER_THREAD; ++e) {
+    const long long x = base + e * EW_THREADS + threadIdx.x;
+    if (x >= J.N) break;
     float2 y[P_];
 #pragma unroll
-    for (int j = 0; j < P_; ++j) y[j] = Y[j * stride + x];
+    for (int j = 0; j < P_; ++j) y[j] = J.b[j * J.stride + x];
     float sc = 1.0f;
 #pragma unroll
     for (int q = 1; q <= P_; ++q) {
       sc *= 0.5f;
-      float2 acc = Z[(q - 1) * stride + x];
+      float2 acc = J.a[(q - 1) * J.stride + x];
 #pragma unroll
       for (int j = 1; j <= q; ++j) {
         const int d = q - j;
@@ -170,60 +204,37 @@ __global__ void ff_squaring_kernel(const float2* __restrict__ Z, const float2* _
       }
       acc.x *= sc;
       acc.y *= sc;
-      if (OUT_F64)
-        reinterpret_cast<double*>(Yn)[(q - 1) * stride + x] = ff_to_f64(acc.x, acc.y);
+      if (J.out_f64)
+        reinterpret_cast<double*>(out)[(q - 1) * J.stride + x] = ff_to_f64(acc.x, acc.y);
       else
-        reinterpret_cast<float2*>(Yn)[(q - 1) * stride + x] = acc;
-      if (acc.x != 0.f) emax[q - 1] = max(emax[q - 1], exp_plus1(acc.x));
+        reinterpret_cast<float2*>(out)[(q - 1) * J.stride + x] = acc;
+      if (out2) reinterpret_cast<double*>(out2)[(q - 1) * J.stride + x] = ff_to_f64(acc.x, acc.y);
+      emax[q - 1] = max(emax[q - 1], (int)((__float_as_uint(acc.x) >> 23) & 0xFFu));
     }
   }
-  if (!OUT_F64) {
+  if (J.out_exp) {
 #pragma unroll
-    for (int j = 0; j < P_; ++j) warp_max_atomic(emax[j], out_exp ? out_exp + j : nullptr);
+    for (int j = 0; j < P_; ++j) warp_max_atomic(emax[j] > 0 ? emax[j] - 126 : -1000, J.out_exp + j);
   }
 }
 
-__global__ void f64_exponent_kernel(const double* __restrict__ v, long long N, int* __restrict__ slot) {
+// e with |v| < 2^e over a float64 vector (integer ops only), grouped over jobs
+__global__ void __launch_bounds__(EW_THREADS) g_expscan_kernel(const EJob* __restrict__ jobs, int njobs,
+                                                               const void* const* ptrtab) {
+  const int jb = find_ejob(jobs, njobs, blockIdx.x);
+  const EJob& J = jobs[jb];
+  const double* v = reinterpret_cast<const double*>(tab_ptr(ptrtab, J.v_tab, J.tab_off_v, (void*)J.v));
   int e = -1000;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long base = (blockIdx.x - J.block_begin) * EW_BLOCK;
+#pragma unroll
+  for (int q = 0; q < EW_PER_THREAD; ++q) {
+    const long long i = base + q * EW_THREADS + threadIdx.x;
+    if (i >= J.N) break;
     const uint64_t b = (uint64_t)__double_as_longlong(v[i]);
     const int ex = (int)((b >> 52) & 0x7FF);
     if (ex != 0) e = max(e, ex - 1022);  // |x| < 2^{ex - 1023 + 1}
   }
-  warp_max_atomic(e, slot);
-}
-
-int ew_grid(long long N) {
-  long long b = (N + 255) / 256;
-  return (int)std::max(1LL, std::min(b, 152LL * 8));
-}
-
-template <int P_>
-int launch_ws(const float2* T, long long Ts, const float2* coef, int m, long long N, void* Y, long long Ys,
-              int out_f64, int* out_exp, cudaStream_t st) {
-  const size_t sm = sizeof(float2) * P_ * m;
-  launch_begin(KC_WEIGHTED, st);
-  if (out_f64)
-    ff_weighted_sum_kernel<P_, true><<<ew_grid(N), 256, sm, st>>>(T, Ts, coef, m, N, Y, Ys, out_exp);
-  else
-    ff_weighted_sum_kernel<P_, false><<<ew_grid(N), 256, sm, st>>>(T, Ts, coef, m, N, Y, Ys, out_exp);
-  launch_end(st);
-  PK_CHECK_LAUNCH();
-  return PHIKRON_OK;
-}
-
-template <int P_>
-int launch_sq(const float2* Z, const float2* Y, void* Yn, long long N, long long stride, int out_f64,
-              int* out_exp, const InvFact& inv, cudaStream_t st) {
-  launch_begin(KC_SQUARING, st);
-  if (out_f64)
-    ff_squaring_kernel<P_, true><<<ew_grid(N), 256, 0, st>>>(Z, Y, Yn, N, stride, out_exp, inv);
-  else
-    ff_squaring_kernel<P_, false><<<ew_grid(N), 256, 0, st>>>(Z, Y, Yn, N, stride, out_exp, inv);
-  launch_end(st);
-  PK_CHECK_LAUNCH();
-  return PHIKRON_OK;
+  warp_max_atomic(e, J.out_exp);
 }
 
 InvFact make_invfact() {
@@ -238,61 +249,63 @@ InvFact make_invfact() {
   return r;
 }
 
-}  // namespace
-
-#define PK_DISPATCH_P(p, CALL)                                                                     \
-  switch (p) {                                                                                     \
-    case 1: { constexpr int PP = 1; return CALL; }                                                 \
-    case 2: { constexpr int PP = 2; return CALL; }                                                 \
-    case 3: { constexpr int PP = 3; return CALL; }                                                 \
-    case 4: { constexpr int PP = 4; return CALL; }                                                 \
-    case 5: { constexpr int PP = 5; return CALL; }                                                 \
-    case 6: { constexpr int PP = 6; return CALL; }                                                 \
-    case 7: { constexpr int PP = 7; return CALL; }                                                 \
-    case 8: { constexpr int PP = 8; return CALL; }                                                 \
-    default: set_error("mixed path: l_max must be <= 8"); return PHIKRON_ENOTSUP;                  \
+template <int P_>
+int launch_ew(int kind, const EJob* jobs, int njobs, long long blocks, const void* const* tab, cudaStream_t st) {
+  if (kind == STEP_WEIGHTED) {
+    launch_begin(KC_WEIGHTED, st);
+    g_weighted_kernel<P_><<<(unsigned)blocks, EW_THREADS, 0, st>>>(jobs, njobs, tab);
+  } else {
+    static const InvFact inv = make_invfact();
+    launch_begin(KC_SQUARING, st);
+    g_squaring_kernel<P_><<<(unsigned)blocks, EW_THREADS, 0, st>>>(jobs, njobs, tab, inv);
   }
-
-int ff_weighted_sum(const float2* T, long long T_stride, const float2* coef, int p, int m, long long N,
-                    void* Y, long long Y_stride, int out_f64, int* out_exp, cudaStream_t st) {
-  PK_DISPATCH_P(p, launch_ws<PP>(T, T_stride, coef, m, N, Y, Y_stride, out_f64, out_exp, st));
-}
-
-int ff_squaring_combine(const float2* Z, const float2* Y, void* Yn, int p, long long N, long long stride,
-                        int out_f64, int* out_exp, cudaStream_t st) {
-  static const InvFact inv = make_invfact();
-  PK_DISPATCH_P(p, launch_sq<PP>(Z, Y, Yn, N, stride, out_f64, out_exp, inv, st));
-}
-
-int f64_exponent(const double* v, long long N, int* slot, cudaStream_t st) {
-  launch_begin(KC_CONVERT, st);
-  f64_exponent_kernel<<<ew_grid(N), 256, 0, st>>>(v, N, slot);
   launch_end(st);
   PK_CHECK_LAUNCH();
   return PHIKRON_OK;
 }
 
+int launch_ew_p(int kind, int p, const EJob* jobs, int njobs, long long blocks, const void* const* tab,
+                cudaStream_t st) {
+  switch (p) {
+    case 1: return launch_ew<1>(kind, jobs, njobs, blocks, tab, st);
+    case 2: return launch_ew<2>(kind, jobs, njobs, blocks, tab, st);
+    case 3: return launch_ew<3>(kind, jobs, njobs, blocks, tab, st);
+    case 4: return launch_ew<4>(kind, jobs, njobs, blocks, tab, st);
+    case 5: return launch_ew<5>(kind, jobs, njobs, blocks, tab, st);
+    case 6: return launch_ew<6>(kind, jobs, njobs, blocks, tab, st);
+    case 7: return launch_ew<7>(kind, jobs, njobs, blocks, tab, st);
+    case 8: return launch_ew<8>(kind, jobs, njobs, blocks, tab, st);
+    default: set_error("mixed path: l_max must be in 1..8"); return PHIKRON_ENOTSUP;
+  }
+}
+
+}  // namespace
+
 // ----------------------------------------------------------------------------- host slicing
 
 size_t sliced_bytes(int n, int slices) {
   const int nchunks = (n + KC - 1) / KC;
-  return (size_t)nchunks * slices * SLICE_BYTES;
+  const int nhalves = (n + 127) / 128;
+  return (size_t)nhalves * nchunks * slices * SLICE_BYTES;
 }
 
+// E (n x n, n <= 256) -> [half][chunk32][slice][128 rows x 32 cols core-matrix layout] with
+// rows 128*half .. +127 of E in each half; rexp[half*128 + i] = f with max_k |E[row][k]| < 2^f.
+// Digits are those of |E| * 2^{64-f} rounded to nearest at digit `slices`.
 void slice_matrix_host(const double* E, int n, int slices, uint8_t* out, int* rexp) {
   const int nchunks = (n + KC - 1) / KC;
+  const int nhalves = (n + 127) / 128;
   std::memset(out, 0, sliced_bytes(n, slices));
-  for (int i = 0; i < 128; ++i) rexp[i] = 0;
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < 128 * nhalves; ++i) rexp[i] = 0;
+  for (int row = 0; row < n; ++row) {
+    const int h = row / 128, i = row % 128;
     double mx = 0.0;
-    for (int k = 0; k < n; ++k) mx = std::max(mx, std::fabs(E[(size_t)i * n + k]));
+    for (int k = 0; k < n; ++k) mx = std::max(mx, std::fabs(E[(size_t)row * n + k]));
     int f = 0;
-    if (mx > 0.0) {
-      std::frexp(mx, &f);  // mx = frac * 2^f, frac in [0.5, 1) -> mx < 2^f
-    }
-    rexp[i] = f;
+    if (mx > 0.0) std::frexp(mx, &f);  // mx = frac * 2^f, frac in [0.5, 1) -> mx < 2^f
+    rexp[h * 128 + i] = f;
     for (int k = 0; k < n; ++k) {
-      const double x = E[(size_t)i * n + k];
+      const double x = E[(size_t)row * n + k];
       const double a = std::ldexp(std::fabs(x), 64 - f);  // in [0, 2^64)
       uint64_t F = (a >= 18446744073709551616.0) ? ~0ull : (uint64_t)a;
       const uint64_t half = 1ull << (63 - 8 * slices);  // round to nearest at the last digit
@@ -307,7 +320,7 @@ void slice_matrix_host(const double* E, int n, int slices, uint8_t* out, int* re
         uint32_t bits;
         std::memcpy(&bits, &v, 4);
         const uint16_t bf = (uint16_t)(bits >> 16);
-        uint8_t* dst = out + ((size_t)c * slices + s) * SLICE_BYTES + off;
+        uint8_t* dst = out + (((size_t)h * nchunks + c) * slices + s) * SLICE_BYTES + off;
         std::memcpy(dst, &bf, 2);
       }
     }
@@ -319,16 +332,29 @@ void slice_matrix_host(const double* E, int n, int slices, uint8_t* out, int* re
 struct MixedState {
   int slices = 5;
   int nsm = 148;
-  uint8_t* dSl[3] = {nullptr, nullptr, nullptr};  // per unique factor: nexp matrices
-  int* dRexp[3] = {nullptr, nullptr, nullptr};
+  uint8_t* dSl[3] = {nullptr, nullptr, nullptr};  // per unique factor: nexp sliced matrices
+  int* dRexp[3] = {nullptr, nullptr, nullptr};     // per unique factor: nexp x nhalves x 128
   size_t mat_bytes[3] = {0, 0, 0};
+  int rexp_stride[3] = {128, 128, 128};
   float2* dCoefFF = nullptr;
-  int* dSlots = nullptr;
-  int nslots = 0;
-  int* dStatus = nullptr;
+  Seq seq;                                         // launch sequence of a single-vector apply
 };
 
 static void mixed_free(void* p) { delete static_cast<MixedState*>(p); }
+
+const MixedView mixed_view(const Plan& P, int d) {
+  const MixedState& M = *static_cast<const MixedState*>(P.mixed);
+  const int u = P.uniq_of[d];
+  MixedView v;
+  v.sl = M.dSl[u];
+  v.rexp = M.dRexp[u];
+  v.mat_bytes = M.mat_bytes[u];
+  v.rexp_stride = M.rexp_stride[u];
+  v.coef = M.dCoefFF;
+  v.slices = M.slices;
+  v.nsm = M.nsm;
+  return v;
+}
 
 int precision_setup(Plan& P) {
   if (P.opts.precision == PHIKRON_PREC_FP64) return PHIKRON_OK;
@@ -337,22 +363,20 @@ int precision_setup(Plan& P) {
     return PHIKRON_ENOTSUP;
   }
   for (int d = 0; d < P.dims; ++d) {
-    if (P.n[d] < 16 || P.n[d] > 128 || P.n[d] % 16 != 0) {
-      set_error("mixed path: every n[d] must be a multiple of 16 in 16..128");
+    if (P.n[d] < 16 || P.n[d] > 256 || P.n[d] % 16 != 0) {
+      set_error("mixed path: every n[d] must be a multiple of 16 in 16..256");
       return PHIKRON_ENOTSUP;
     }
   }
-  if (P.p > 8) {
-    set_error("mixed path: l_max must be <= 8");
+  if (P.p > MAXP || P.m > MAXM) {
+    set_error("mixed path: needs l_max <= 8 and at most 64 quadrature nodes");
     return PHIKRON_ENOTSUP;
   }
   MixedState* M = new MixedState();
   P.mixed = M;
   P.mixed_free = mixed_free;
   int slices = P.opts.slices;
-  if (slices <= 0) {
-    slices = (P.tol >= 1e-5) ? 3 : (P.tol >= 1e-7) ? 4 : (P.tol >= 1e-10) ? 5 : 6;
-  }
+  if (slices <= 0) slices = (P.tol >= 1e-5) ? 3 : (P.tol >= 1e-7) ? 4 : (P.tol >= 1e-10) ? 5 : 6;
   if (slices < 3 || slices > 6) {
     set_error("mixed path: slices must be 3..6");
     return PHIKRON_EINVAL;
@@ -369,14 +393,17 @@ int precision_setup(Plan& P) {
     std::vector<double> h(nn * P.nexp);
     PK_TRY_CUDA(cudaMemcpy(h.data(), P.dExp[u], sizeof(double) * nn * P.nexp, cudaMemcpyDeviceToHost));
     const size_t mb = sliced_bytes(nd, slices);
+    const int rs = 128 * ((nd + 127) / 128);
     std::vector<uint8_t> sl(mb * P.nexp);
-    std::vector<int> rx(128 * P.nexp);
-    for (int e = 0; e < P.nexp; ++e) slice_matrix_host(h.data() + nn * e, nd, slices, sl.data() + mb * e, rx.data() + 128 * e);
+    std::vector<int> rx((size_t)rs * P.nexp);
+    for (int e = 0; e < P.nexp; ++e)
+      slice_matrix_host(h.data() + nn * e, nd, slices, sl.data() + mb * e, rx.data() + (size_t)rs * e);
     PK_RET(P.alloc((void**)&M->dSl[u], sl.size()));
     PK_RET(P.alloc((void**)&M->dRexp[u], sizeof(int) * rx.size()));
     PK_TRY_CUDA(cudaMemcpy(M->dSl[u], sl.data(), sl.size(), cudaMemcpyHostToDevice));
     PK_TRY_CUDA(cudaMemcpy(M->dRexp[u], rx.data(), sizeof(int) * rx.size(), cudaMemcpyHostToDevice));
     M->mat_bytes[u] = mb;
+    M->rexp_stride[u] = rs;
   }
   // node weights as float-float
   std::vector<float2> cf(P.coef.size());
@@ -387,138 +414,34 @@ int precision_setup(Plan& P) {
   PK_RET(P.alloc((void**)&M->dCoefFF, sizeof(float2) * std::max<size_t>(1, cf.size())));
   if (!cf.empty())
     PK_TRY_CUDA(cudaMemcpy(M->dCoefFF, cf.data(), sizeof(float2) * cf.size(), cudaMemcpyHostToDevice));
-  // exponent slots: v + per pass per vector + Y + per squaring step
-  const int nv = std::max(P.m + 1, std::max(P.p, 1));
-  M->nslots = 1 + 3 * nv + P.p + P.s * (3 * P.p + P.p) + 16;
-  PK_RET(P.alloc((void**)&M->dSlots, sizeof(int) * M->nslots));
-  PK_RET(P.alloc((void**)&M->dStatus, sizeof(int)));
-  PK_TRY_CUDA(cudaMemset(M->dStatus, 0, sizeof(int)));
+
+  // the single-vector apply as a launch sequence over the plan's own work buffers
+  std::vector<SeqUnit> units(1);
+  units[0].plan = &P;
+  units[0].inst = 0;
+  units[0].rhs = 0;
+  units[0].W1 = reinterpret_cast<float2*>(P.dW1);
+  units[0].W2 = reinterpret_cast<float2*>(P.dW2);
+  units[0].Y = reinterpret_cast<float2*>(P.dY);
+  units[0].Yn = reinterpret_cast<float2*>(P.dYn);
+  SeqConfig cfg;
+  cfg.half = P.opts.half_step != 0;
+  cfg.slices = slices;
+  cfg.sub = 1;
+  cfg.grid = M->nsm;
+  cfg.big_first = false;
+  cfg.graph = true;
+  PK_RET(seq_build(M->seq, units, 1, cfg));
   return PHIKRON_OK;
 }
-
-namespace {
-
-struct ChainVec {
-  const void* in;       // input of the first pass
-  int in_slot;          // slot index of the input exponent
-  int mat;              // matrix index e in the per-factor exponential arrays
-  void* out;            // final destination
-  bool out_f64;         // final destination is float64
-  int out_slot;         // slot index for the final output exponent (-1: none)
-};
-
-// Kronecker action (x)_d E_d on a batch of vectors, one pass per axis (Eq. (8)).
-int kron_chain_mixed(Plan& P, MixedState& M, const std::vector<ChainVec>& vecs, bool first_in_f64,
-                     float2* bufA, float2* bufB, int& slot_next, cudaStream_t st) {
-  const long long N = P.N;
-  const int nvec = (int)vecs.size();
-  std::vector<int> cur_slot(nvec);
-  for (int j = 0; j < nvec; ++j) cur_slot[j] = vecs[j].in_slot;
-  for (int d = 0; d < P.dims; ++d) {
-    long long B0 = 1, R = 1;
-    for (int q = 0; q < d; ++q) B0 *= P.n[q];
-    for (int q = d + 1; q < P.dims; ++q) R *= P.n[q];
-    const int u = P.uniq_of[d];
-    const bool last = (d == P.dims - 1);
-    float2* dstbuf = (d % 2 == 0) ? bufA : bufB;
-    const float2* srcbuf = (d % 2 == 0) ? bufB : bufA;
-    for (int j0 = 0; j0 < nvec; j0 += MAX_MODE_JOBS) {
-      ModePass pass{};
-      pass.n = P.n[d];
-      pass.R = R;
-      pass.B0 = B0;
-      pass.in_f64 = (d == 0) ? (first_in_f64 ? 1 : 0) : 0;
-      const int cnt = std::min(MAX_MODE_JOBS, nvec - j0);
-      pass.njobs = cnt;
-      for (int q = 0; q < cnt; ++q) {
-        const int j = j0 + q;
-        ModeJob& J = pass.jobs[q];
-        J.in = (d == 0) ? vecs[j].in : (const void*)(srcbuf + (size_t)j * N);
-        J.in_exp = M.dSlots + cur_slot[j];
-        J.eslices = M.dSl[u] + M.mat_bytes[u] * (size_t)vecs[j].mat;
-        J.rexp = M.dRexp[u] + 128 * vecs[j].mat;
-        if (last) {
-          J.out = vecs[j].out;
-          J.out_f64 = vecs[j].out_f64 ? 1 : 0;
-          J.out_exp = (vecs[j].out_slot >= 0) ? M.dSlots + vecs[j].out_slot : nullptr;
-        } else {
-          J.out = dstbuf + (size_t)j * N;
-          J.out_f64 = 0;
-          J.out_exp = M.dSlots + slot_next + j;
-        }
-      }
-      PK_RET(tc::mode_pass(pass, M.slices, M.dStatus, M.nsm, st));
-    }
-    if (!last) {
-      for (int j = 0; j < nvec; ++j) cur_slot[j] = slot_next + j;
-      slot_next += nvec;
-    }
-  }
-  return PHIKRON_OK;
-}
-
-}  // namespace
 
 int apply_mixed(Plan& P, const double* V, double* Out, cudaStream_t st) {
   MixedState& M = *static_cast<MixedState*>(P.mixed);
-  const long long N = P.N;
-  const int p = P.p, m = P.m, s = P.s;
-  float2* W1 = reinterpret_cast<float2*>(P.dW1);
-  float2* W2 = reinterpret_cast<float2*>(P.dW2);
-  float2* Y = reinterpret_cast<float2*>(P.dY);
-  float2* Yn = reinterpret_cast<float2*>(P.dYn);
-  PK_TRY_CUDA(cudaMemsetAsync(M.dSlots, 0x80, sizeof(int) * M.nslots, st));
-  PK_RET(f64_exponent(V, N, M.dSlots + 0, st));
-  int slot_next = 1;
-  // chain buffers: the last pass writes the chain's destination, so intermediates must
-  // avoid it; with dims passes the intermediates alternate bufA (d even) / bufB (d odd).
-  // node phase destination for the m node actions: W1 when dims is odd (last pass d=dims-1
-  // even -> writes bufA... ) -- choose the pair so the destination is never an input.
-  std::vector<ChainVec> vecs;
-  if (p == 0) {
-    vecs.push_back({V, 0, m, Out, true, -1});
-    return kron_chain_mixed(P, M, vecs, true, W1, W2, slot_next, st);
-  }
-  // node actions (k < m) to T, phi_0 (matrix index m = exp(M^d)) straight to Out[0]
-  // intermediates: d=0 -> bufA, d=1 -> bufB, final (d = dims-1) -> destination.
-  // dims = 3: bufA = W1, bufB = W2, destination T = W1 (read from W2 in the last pass).
-  // dims = 2: bufA = W1, destination T = W2 (read from W1).
-  float2* T = (P.dims == 3) ? W1 : W2;
-  const int slotT = slot_next;
-  slot_next += m;
-  for (int k = 0; k < m; ++k) vecs.push_back({V, 0, k, T + (size_t)k * N, false, slotT + k});
-  vecs.push_back({V, 0, m, Out, true, -1});
-  PK_RET(kron_chain_mixed(P, M, vecs, true, W1, W2, slot_next, st));
-  // weighted sums over the nodes (Algorithm 1, second step)
-  const int slotY = slot_next;
-  slot_next += p;
-  if (s == 0) {
-    return ff_weighted_sum(T, N, M.dCoefFF, p, m, N, Out + N, N, 1, nullptr, st);
-  }
-  PK_RET(ff_weighted_sum(T, N, M.dCoefFF, p, m, N, Y, N, 0, M.dSlots + slotY, st));
-  int ycur = slotY;
-  for (int t = 0; t < s; ++t) {
-    // Z_i = (x)_d G_{t,d} y_i, i = 1..p
-    std::vector<ChainVec> zv;
-    float2* Z = (P.dims == 3) ? W1 : W2;
-    for (int i = 0; i < p; ++i) zv.push_back({Y + (size_t)i * N, ycur + i, m + 1 + t, Z + (size_t)i * N, false, -1});
-    PK_RET(kron_chain_mixed(P, M, zv, false, W1, W2, slot_next, st));
-    const bool last = (t == s - 1);
-    const int slotYn = slot_next;
-    slot_next += p;
-    if (last) {
-      PK_RET(ff_squaring_combine(Z, Y, Out + N, p, N, N, 1, nullptr, st));
-    } else {
-      PK_RET(ff_squaring_combine(Z, Y, Yn, p, N, N, 0, M.dSlots + slotYn, st));
-      std::swap(Y, Yn);
-      ycur = slotYn;
-    }
-  }
-  if (slot_next > M.nslots) {
-    set_error("mixed path: exponent slot overflow");
-    return PHIKRON_EINVAL;
-  }
-  return PHIKRON_OK;
+  PtrArgs args{};
+  args.n = 2;
+  args.p[0] = const_cast<double*>(V);
+  args.p[1] = Out;
+  return seq_run(M.seq, args, st);
 }
 
 int mixed_slices(const Plan& P) { return static_cast<const MixedState*>(P.mixed)->slices; }
@@ -529,8 +452,416 @@ int mixed_status(Plan& P, int* status) {
     return PHIKRON_OK;
   }
   MixedState& M = *static_cast<MixedState*>(P.mixed);
-  PK_TRY_CUDA(cudaMemcpy(status, M.dStatus, sizeof(int), cudaMemcpyDeviceToHost));
-  PK_TRY_CUDA(cudaMemset(M.dStatus, 0, sizeof(int)));
+  return seq_status(M.seq, status);
+}
+
+// ----------------------------------------------------------------------------- sequences
+
+Seq::~Seq() {
+  if (exec) cudaGraphExecDestroy(exec);
+  for (void* p : allocs) cudaFree(p);
+}
+
+namespace {
+
+int seq_alloc(Seq& S, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    return PHIKRON_ENOMEM;
+  }
+  S.allocs.push_back(*p);
+  S.device_bytes += bytes;
+  return PHIKRON_OK;
+}
+
+long long job_tiles(const GJob& j, bool trans) {
+  const long long halves = (j.n + 127) / 128;
+  return trans ? halves * j.B0 * ((j.R + 127) / 128) : halves * ((j.B0 + 127) / 128);
+}
+
+struct Builder {
+  std::vector<GJob> gjobs;
+  std::vector<EJob> ejobs;
+  std::vector<Step> steps;
+  int nslots = 0;
+  bool big_first = false;
+
+  void mode_step(std::vector<GJob> jobs, const PassShape& shape) {
+    if (jobs.empty()) return;
+    if (big_first)
+      std::stable_sort(jobs.begin(), jobs.end(), [&](const GJob& a, const GJob& b) {
+        return job_tiles(a, shape.trans) > job_tiles(b, shape.trans);
+      });
+    long long t = 0;
+    for (GJob& j : jobs) {
+      j.tile_begin = t;
+      t += job_tiles(j, shape.trans);
+    }
+    Step s{};
+    s.kind = STEP_MODE;
+    s.off = gjobs.size();
+    s.count = (int)jobs.size();
+    s.total = t;
+    s.shape = shape;
+    gjobs.insert(gjobs.end(), jobs.begin(), jobs.end());
+    steps.push_back(s);
+  }
+
+  void ew_step(int kind, std::vector<EJob> jobs, int p) {
+    if (jobs.empty()) return;
+    long long b = 0;
+    for (EJob& j : jobs) {
+      j.block_begin = b;
+      b += (j.N + EW_BLOCK - 1) / EW_BLOCK;
+    }
+    Step s{};
+    s.kind = kind;
+    s.off = ejobs.size();
+    s.count = (int)jobs.size();
+    s.total = b;
+    s.p = p;
+    ejobs.insert(ejobs.end(), jobs.begin(), jobs.end());
+    steps.push_back(s);
+  }
+};
+
+}  // namespace
+
+// Builds the launch sequence of Algorithm 1 + Algorithm 6 (+ phi_0, + optional half-step
+// outputs) over `units` (one unit = one vector of one plan).  Unit u reads V from pointer
+// table entry 2*inst at byte offset rhs*N*8 and writes Out to entry 2*inst+1 at offset
+// rhs*(p+1)*(1+half)*N*8.
+int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& cfg) {
+  Builder B;
+  B.big_first = cfg.big_first;
+  const int nu = (int)units.size();
+  if (nu == 0) return PHIKRON_OK;
+  const int dims = units[0].plan->dims;
+  const int p = units[0].plan->p;
+  for (const SeqUnit& U : units) {
+    if (U.plan->dims != dims || U.plan->p != p) {
+      set_error("batched apply: every plan must have the same dims and l_max");
+      return PHIKRON_EINVAL;
+    }
+  }
+  if (2 * ninst > MAX_PTRS) {
+    set_error("batched apply: at most 64 plans");
+    return PHIKRON_EINVAL;
+  }
+  S.p = p;
+  S.half = cfg.half;
+  S.ninst = ninst;
+  // per-unit exponent slots
+  std::vector<int> slot0(nu);
+  for (int u = 0; u < nu; ++u) {
+    const Plan& P = *units[u].plan;
+    slot0[u] = B.nslots;
+    const int nv = P.m + 2;
+    B.nslots += 1 + nv * dims + p + P.s * (dims * p + p) + 8;
+  }
+  // placeholders for device pointers: slots are resolved after allocation (offsets now)
+  PK_RET(seq_alloc(S, (void**)&S.dSlots, sizeof(int) * B.nslots));
+  PK_RET(seq_alloc(S, (void**)&S.dPtrtab, sizeof(void*) * MAX_PTRS));
+  PK_RET(seq_alloc(S, (void**)&S.dStatus, sizeof(int)));
+  PK_TRY_CUDA(cudaMemset(S.dStatus, 0, sizeof(int)));
+  S.nslots = B.nslots;
+  int* slots = S.dSlots;
+
+  struct UState {
+    int next;              // next free slot
+    int vslot;
+    float2* Y;
+    float2* Yn;
+    int yslot;
+  };
+  std::vector<UState> us(nu);
+  for (int u = 0; u < nu; ++u) {
+    us[u].next = slot0[u];
+    us[u].vslot = us[u].next++;
+    us[u].Y = units[u].Y;
+    us[u].Yn = units[u].Yn;
+  }
+  const long long out_mult = (long long)(p + 1) * (cfg.half ? 2 : 1);
+
+  // 1. exponent scan of every input vector
+  {
+    std::vector<EJob> ej;
+    for (int u = 0; u < nu; ++u) {
+      const Plan& P = *units[u].plan;
+      EJob j{};
+      j.N = P.N;
+      j.v_tab = 2 * units[u].inst;
+      j.tab_off_v = (long long)units[u].rhs * P.N * 8;
+      j.out_tab = j.out2_tab = -1;
+      j.out_exp = slots + us[u].vslot;
+      ej.push_back(j);
+    }
+    B.ew_step(STEP_EXPSCAN, ej, p);
+  }
+
+  // generic Kronecker chain over a list of (unit, matrix index, input, output) vectors
+  struct CV {
+    int u, mat;
+    const void* in;        // direct input (pass 0) or null for table input
+    int in_slot;
+    bool in_tab;           // pass-0 input is V (table)
+    int vec;               // index of the vector within the unit's W buffers
+    void* out;             // final destination (direct) or null for table output
+    bool out_tab;
+    long long out_off;     // byte offset within Out (table) when out_tab
+    bool out_f64;
+    int out_slot;          // -1 none
+  };
+  auto chain = [&](const std::vector<CV>& vs, bool first_f64) -> int {
+    std::vector<int> cur(vs.size());
+    for (size_t q = 0; q < vs.size(); ++q) cur[q] = vs[q].in_slot;
+    for (int d = 0; d < dims; ++d) {
+      const bool last = (d == dims - 1);
+      std::vector<GJob> jobs;
+      std::vector<int> newslot(vs.size(), -1);
+      bool trans = false;
+      for (size_t q = 0; q < vs.size(); ++q) {
+        const CV& c = vs[q];
+        const Plan& P = *units[c.u].plan;
+        long long B0 = 1, R = 1;
+        for (int e = 0; e < d; ++e) B0 *= P.n[e];
+        for (int e = d + 1; e < dims; ++e) R *= P.n[e];
+        trans = R > 1;
+        const MixedView mv = mixed_view(P, d);
+        const long long N = P.N;
+        float2* dst = (d % 2 == 0) ? units[c.u].W1 : units[c.u].W2;
+        const float2* src = (d % 2 == 0) ? units[c.u].W2 : units[c.u].W1;
+        GJob j{};
+        j.n = P.n[d];
+        j.R = R;
+        j.B0 = B0;
+        j.eslices = mv.sl + mv.mat_bytes * (size_t)c.mat;
+        j.rexp = mv.rexp + (size_t)mv.rexp_stride * c.mat;
+        j.in_tab = -1;
+        j.out_tab = -1;
+        if (d == 0) {
+          if (c.in_tab) {
+            j.in_tab = 2 * units[c.u].inst;
+            j.tab_off_in = (long long)units[c.u].rhs * N * 8;
+          } else {
+            j.in = c.in;
+          }
+        } else {
+          j.in = src + (size_t)c.vec * N;
+        }
+        j.in_exp = slots + cur[q];
+        if (last) {
+          if (c.out_tab) {
+            j.out_tab = 2 * units[c.u].inst + 1;
+            j.tab_off_out = (long long)units[c.u].rhs * out_mult * N * 8 + c.out_off;
+          } else {
+            j.out = c.out;
+          }
+          j.out_f64 = c.out_f64 ? 1 : 0;
+          j.out_exp = c.out_slot >= 0 ? slots + c.out_slot : nullptr;
+        } else {
+          j.out = dst + (size_t)c.vec * N;
+          j.out_f64 = 0;
+          newslot[q] = us[c.u].next++;
+          j.out_exp = slots + newslot[q];
+        }
+        jobs.push_back(j);
+      }
+      PassShape sh;
+      sh.slices = cfg.slices;
+      sh.sub = cfg.sub;
+      sh.grid = cfg.grid;
+      sh.in_f64 = (d == 0) && first_f64;
+      sh.trans = trans;
+      if (dims == 1) sh.trans = false;
+      // all jobs of one pass share the formulation (same axis d)
+      B.mode_step(jobs, sh);
+      for (size_t q = 0; q < vs.size(); ++q)
+        if (newslot[q] >= 0) cur[q] = newslot[q];
+    }
+    return PHIKRON_OK;
+  };
+
+  // 2. node phase: m node actions (to T), phi_0 (to Out[0]), half-step phi_0 (to Out[p+1])
+  std::vector<float2*> T(nu);
+  std::vector<int> tslot(nu);
+  {
+    std::vector<CV> vs;
+    for (int u = 0; u < nu; ++u) {
+      const Plan& P = *units[u].plan;
+      T[u] = (dims % 2 == 1) ? units[u].W1 : units[u].W2;
+      tslot[u] = us[u].next;
+      us[u].next += P.m;
+      for (int k = 0; k < P.m; ++k)
+        vs.push_back(CV{u, k, nullptr, us[u].vslot, true, k, T[u] + (size_t)k * P.N, false, 0, false, tslot[u] + k});
+      vs.push_back(CV{u, P.m, nullptr, us[u].vslot, true, P.m, nullptr, true, 0, true, -1});
+      if (cfg.half)
+        vs.push_back(CV{u, P.m + P.s, nullptr, us[u].vslot, true, P.m + 1, nullptr, true,
+                        (long long)(p + 1) * P.N * 8, true, -1});
+    }
+    PK_RET(chain(vs, true));
+  }
+  if (p >= 1) {
+    // 3. weighted sums
+    std::vector<EJob> ej;
+    for (int u = 0; u < nu; ++u) {
+      const Plan& P = *units[u].plan;
+      const MixedView mv = mixed_view(P, 0);
+      EJob j{};
+      j.a = T[u];
+      j.coef = mv.coef;
+      j.m = P.m;
+      j.N = P.N;
+      j.stride = P.N;
+      j.out_tab = j.out2_tab = -1;
+      if (P.s == 0) {
+        j.out_tab = 2 * units[u].inst + 1;
+        j.tab_off_out = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)P.N * 8;
+        j.out_f64 = 1;
+      } else {
+        j.out = us[u].Y;
+        us[u].yslot = us[u].next;
+        us[u].next += p;
+        j.out_exp = slots + us[u].yslot;
+      }
+      if (cfg.half && P.s == 1) {
+        j.out2_tab = 2 * units[u].inst + 1;
+        j.tab_off_out2 = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)(p + 2) * P.N * 8;
+      }
+      ej.push_back(j);
+    }
+    B.ew_step(STEP_WEIGHTED, ej, p);
+    // 4. squaring steps (units with s > t take part in step t)
+    int smax = 0;
+    for (int u = 0; u < nu; ++u) smax = std::max(smax, units[u].plan->s);
+    for (int t = 0; t < smax; ++t) {
+      std::vector<CV> vs;
+      std::vector<int> part;
+      for (int u = 0; u < nu; ++u) {
+        const Plan& P = *units[u].plan;
+        if (P.s <= t) continue;
+        part.push_back(u);
+        float2* Z = (dims % 2 == 1) ? units[u].W1 : units[u].W2;
+        for (int i = 0; i < p; ++i)
+          vs.push_back(CV{u, P.m + 1 + t, us[u].Y + (size_t)i * P.N, us[u].yslot + i, false, i,
+                          Z + (size_t)i * P.N, false, 0, false, -1});
+      }
+      PK_RET(chain(vs, false));
+      std::vector<EJob> sj;
+      for (int u : part) {
+        const Plan& P = *units[u].plan;
+        EJob j{};
+        j.a = (dims % 2 == 1) ? units[u].W1 : units[u].W2;
+        j.b = us[u].Y;
+        j.N = P.N;
+        j.stride = P.N;
+        j.out_tab = j.out2_tab = -1;
+        const bool lastt = (t == P.s - 1);
+        if (lastt) {
+          j.out_tab = 2 * units[u].inst + 1;
+          j.tab_off_out = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)P.N * 8;
+          j.out_f64 = 1;
+        } else {
+          j.out = us[u].Yn;
+          const int ns = us[u].next;
+          us[u].next += p;
+          j.out_exp = slots + ns;
+          us[u].yslot = ns;
+        }
+        if (cfg.half && t == P.s - 2) {
+          j.out2_tab = 2 * units[u].inst + 1;
+          j.tab_off_out2 = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)(p + 2) * P.N * 8;
+        }
+        sj.push_back(j);
+        if (!lastt) std::swap(us[u].Y, us[u].Yn);
+      }
+      B.ew_step(STEP_SQUARING, sj, p);
+    }
+  }
+  for (int u = 0; u < nu; ++u) {
+    const Plan& P = *units[u].plan;
+    const int cap = slot0[u] + 1 + (P.m + 2) * dims + p + P.s * (dims * p + p) + 8;
+    if (us[u].next > cap) {
+      set_error("sequence builder: exponent slot overflow");
+      return PHIKRON_EINVAL;
+    }
+  }
+  // upload the job tables
+  PK_RET(seq_alloc(S, (void**)&S.dG, sizeof(GJob) * std::max<size_t>(1, B.gjobs.size())));
+  PK_RET(seq_alloc(S, (void**)&S.dE, sizeof(EJob) * std::max<size_t>(1, B.ejobs.size())));
+  if (!B.gjobs.empty())
+    PK_TRY_CUDA(cudaMemcpy(S.dG, B.gjobs.data(), sizeof(GJob) * B.gjobs.size(), cudaMemcpyHostToDevice));
+  if (!B.ejobs.empty())
+    PK_TRY_CUDA(cudaMemcpy(S.dE, B.ejobs.data(), sizeof(EJob) * B.ejobs.size(), cudaMemcpyHostToDevice));
+  S.steps = B.steps;
+  S.njobs_mode = B.gjobs.size();
+  // capture the sequence as a CUDA graph
+  if (cfg.graph) {
+    cudaStream_t cs;
+    PK_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    ProfScope none(nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int rc = PHIKRON_OK;
+    if (e == cudaSuccess) rc = seq_launch_all(S, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess && rc == PHIKRON_OK && e2 == cudaSuccess && g) {
+      e = cudaGraphInstantiate(&S.exec, g, 0);
+      if (e != cudaSuccess) S.exec = nullptr;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    clear_error();
+  }
+  return PHIKRON_OK;
+}
+
+int seq_launch_all(Seq& S, cudaStream_t st) {
+  PK_TRY_CUDA(cudaMemsetAsync(S.dSlots, 0x80, sizeof(int) * S.nslots, st));
+  for (const Step& s : S.steps) {
+    if (s.kind == STEP_MODE) {
+      GPass P;
+      P.jobs = S.dG + s.off;
+      P.njobs = s.count;
+      P.total_tiles = s.total;
+      P.ptrtab = S.dPtrtab;
+      PK_RET(tc::mode_pass(P, s.shape, S.dStatus, st));
+    } else if (s.kind == STEP_EXPSCAN) {
+      launch_begin(KC_CONVERT, st);
+      g_expscan_kernel<<<(unsigned)s.total, EW_THREADS, 0, st>>>(S.dE + s.off, s.count, S.dPtrtab);
+      launch_end(st);
+      PK_CHECK_LAUNCH();
+    } else {
+      PK_RET(launch_ew_p(s.kind, s.p, S.dE + s.off, s.count, s.total, S.dPtrtab, st));
+    }
+  }
+  return PHIKRON_OK;
+}
+
+int seq_run(Seq& S, const PtrArgs& args, cudaStream_t st) {
+  PK_RET(tc::set_ptrtab(S.dPtrtab, args, st));
+  Profiler* pr = tl_prof;
+  if (S.exec && !(pr && pr->timing)) {
+    PK_TRY_CUDA(cudaGraphLaunch(S.exec, st));
+    if (pr) {
+      pr->launches += (long long)S.steps.size();
+      for (const Step& s : S.steps)
+        pr->launches_by_class[s.kind == STEP_MODE ? KC_TC_MODE
+                              : s.kind == STEP_WEIGHTED ? KC_WEIGHTED
+                              : s.kind == STEP_SQUARING ? KC_SQUARING : KC_CONVERT]++;
+    }
+    return PHIKRON_OK;
+  }
+  return seq_launch_all(S, st);
+}
+
+int seq_status(Seq& S, int* status) {
+  PK_TRY_CUDA(cudaMemcpy(status, S.dStatus, sizeof(int), cudaMemcpyDeviceToHost));
+  PK_TRY_CUDA(cudaMemset(S.dStatus, 0, sizeof(int)));
   return PHIKRON_OK;
 }
 

@@ -7,46 +7,67 @@
 
 namespace phikron {
 
-// One mode product of a pass: out = E x_d in (Eq. (8)), see tc_mode.cu.
-struct ModeJob {
-  const void* in;          // float64 (pass.in_f64) or float2 (hi, lo) vector(s)
+// One mode product (Eq. (8)) of one vector by one matrix, see tc_mode.cu.  Inputs and outputs
+// are either direct device pointers or (tab >= 0) a byte offset into an entry of the pass's
+// device pointer table, which holds the caller's V / Out pointers of the current apply.
+struct GJob {
+  const void* in;          // float64 (pass shape in_f64) or float2 (hi, lo) vector
   const int* in_exp;       // e with |in| < 2^e for the whole vector
-  const uint8_t* eslices;  // E as [chunk][slice][128 rows x 32 K bf16, core-matrix layout]
-  const int* rexp;         // per-row exponents f_i of E (|E[i][k]| < 2^{f_i})
+  const uint8_t* eslices;  // E as [half][chunk32][slice][128 rows x 32 K bf16 core-matrix layout]
+  const int* rexp;         // [half][128] row exponents f_i of E (|E[i][k]| < 2^{f_i})
   void* out;               // float2 or float64 (out_f64)
-  int* out_exp;            // receives max exponent of out (atomicMax), or null
+  int* out_exp;            // receives the max exponent of out (atomicMax), or null
+  long long R, B0;         // product of faster / slower axes than the contracted one
+  long long tile_begin;    // first tile of this job in its pass
+  long long tab_off_in, tab_off_out;  // byte offsets when in_tab / out_tab >= 0
+  int n;                   // contracted size (E is n x n), multiple of 16, <= 256
   int out_f64;
-  int pad_;
+  int in_tab, out_tab;     // pointer-table entries, or -1
 };
 
-constexpr int MAX_MODE_JOBS = 24;
-
-struct ModePass {
-  ModeJob jobs[MAX_MODE_JOBS];
+struct GPass {
+  const GJob* jobs;        // device array, sorted by tile_begin
   int njobs;
-  int n;            // size of the contracted axis (E is n x n)
-  long long R;      // product of the faster axes (1 for the fastest axis)
-  long long B0;     // product of the slower axes
-  int in_f64;       // inputs are float64 (else float-float)
+  long long total_tiles;
+  const void* const* ptrtab;
+};
+
+struct PassShape {
+  int slices;              // digit slices per operand (3..6)
+  int sub;                 // K chunk = 32 * sub (1, or 2 with 3 slices)
+  int grid;                // CTAs (persistent, 1 per SM at most)
+  bool in_f64, trans;
+};
+
+constexpr int MAX_PTRS = 128;
+struct PtrArgs {
+  void* p[MAX_PTRS];
+  int n;
 };
 
 namespace tc {
-int mode_pass(const ModePass& P, int slices, int* status, int nsm, cudaStream_t st);
-}
+int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st);
+int set_ptrtab(void** tab, const PtrArgs& args, cudaStream_t st);
+size_t smem_bytes(int ks, int sub);
+}  // namespace tc
 
-// float-float elementwise kernels (mixed.cu)
-// Y_j = sum_k coef[j][k] T_k (float-float coefficients on the device), j < p, k < m.
-int ff_weighted_sum(const float2* T, long long T_stride, const float2* coef, int p, int m, long long N,
-                    void* Y, long long Y_stride, int out_f64, int* out_exp, cudaStream_t st);
-// Yn_i = 2^{-i}(Z_i + sum_{j<=i} Y_j/(i-j)!), i = 1..p  (Eq. (29)).
-int ff_squaring_combine(const float2* Z, const float2* Y, void* Yn, int p, long long N, long long stride,
-                        int out_f64, int* out_exp, cudaStream_t st);
-// slot = e with |v| < 2^e over a float64 vector (integer ops only).
-int f64_exponent(const double* v, long long N, int* slot, cudaStream_t st);
-
-// Host: cut an n x n float64 matrix into `slices` BF16 digit slices in the kernel's layout.
-// out: nchunks*slices*8192 bytes; rexp: 128 ints (rows >= n get 0).
-void slice_matrix_host(const double* E, int n, int slices, uint8_t* out, int* rexp);
-size_t sliced_bytes(int n, int slices);
+// Grouped float-float elementwise jobs (mixed.cu): weighted sums of Algorithm 1, modified
+// squaring of Eq. (29), and the exponent scan of a float64 input.
+struct EJob {
+  const float2* a;         // weighted: T (m vectors); squaring: Z (p vectors)
+  const float2* b;         // squaring: Y (p vectors); unused for weighted sums
+  const float2* coef;      // weighted: p x m float-float coefficients
+  const double* v;         // exponent scan: float64 input (or table)
+  void* out;               // p vectors (float2), or float64 (out_f64)
+  void* out2;              // optional float64 copy (half-step outputs), or null
+  int* out_exp;            // p slots (float2 outputs), or null
+  long long N, stride;     // vector length; stride between consecutive vectors of a/b/out/out2
+  long long block_begin;   // first block of this job in its launch
+  long long tab_off_out, tab_off_out2, tab_off_v;
+  int m;
+  int out_f64;
+  int out_tab, out2_tab, v_tab;
+  int pad_;
+};
 
 }  // namespace phikron

@@ -64,3 +64,8 @@ int precision_setup(Plan& P);
 int apply_dispatch(Plan& P, int nrhs, const double* V, double* Out, cudaStream_t st);
 
 }  // namespace phikron
+
+// The opaque handle of the C ABI.
+struct phikron_plan_s {
+  phikron::Plan impl;
+};

@@ -38,6 +38,7 @@
 //
 // Every wait on an mbarrier is bounded; on expiry the kernel records PHIKRON_ETIMEOUT in the
 // status word, waits (bounded) for its own tensor-core work, frees its TMEM and returns.
+#include <algorithm>
 #include <cstdint>
 
 #include "common.h"
@@ -228,7 +229,6 @@ __device__ __forceinline__ float pow2f(int e) {
 }
 
 
-}  // namespace
 
 // ---------------------------------------------------------------- the kernel
 
@@ -243,7 +243,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
-// Raw operand values of one thread for one chunk: 8 consecutive k of its operand row.
+// Raw operand values of one thread for one 32-wide K sub-chunk: 8 consecutive k of its row.
 template <bool IN_F64>
 struct Raw {
   double d[IN_F64 ? 8 : 1];
@@ -252,54 +252,79 @@ struct Raw {
 
 struct TileCtx {
   int job;
+  int half;            // which 128-row half of E (n > 128)
+  int n, nsub;         // contracted size, number of 32-wide K sub-chunks
+  long long R, B0;
   long long b0, r0, row0;
   int eX;
   long long in_base, gr;
   bool valid_row;
+  const void* in;
+  void* out;
 };
 
+__device__ __forceinline__ int find_job(const GPass& P, long long tile) {
+  int lo = 0, hi = P.njobs - 1;  // last job with tile_begin <= tile
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.jobs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <bool TRANS>
-__device__ __forceinline__ TileCtx tile_ctx(const ModePass& P, long long tile, long long tiles_per_job,
-                                            long long rtiles, int orow) {
+__device__ __forceinline__ TileCtx tile_ctx(const GPass& P, long long tile, int orow) {
   TileCtx t;
-  t.job = (int)(tile / tiles_per_job);
-  const long long tj = tile % tiles_per_job;
+  t.job = find_job(P, tile);
+  const GJob& J = P.jobs[t.job];
+  t.n = J.n;
+  t.nsub = (J.n + 31) / 32;
+  t.R = J.R;
+  t.B0 = J.B0;
+  const long long tj = tile - J.tile_begin;
+  const long long rtiles = TRANS ? (J.R + 127) / 128 : 1;
+  const long long per_half = TRANS ? J.B0 * rtiles : (J.B0 + 127) / 128;
+  t.half = (int)(tj / per_half);
+  const long long th = tj % per_half;
   t.b0 = t.r0 = t.row0 = 0;
   if (TRANS) {
-    t.b0 = tj / rtiles;
-    t.r0 = (tj % rtiles) * 128;
+    t.b0 = th / rtiles;
+    t.r0 = (th % rtiles) * 128;
   } else {
-    t.row0 = tj * 128;
+    t.row0 = th * 128;
   }
-  int eX = *P.jobs[t.job].in_exp;
+  int eX = *J.in_exp;
   t.eX = eX < -600 ? 0 : eX;  // all-zero input
-  t.in_base = TRANS ? t.b0 * (long long)P.n * P.R : 0;
+  t.in_base = TRANS ? t.b0 * (long long)J.n * J.R : 0;
   t.gr = TRANS ? t.r0 + orow : t.row0 + orow;
-  t.valid_row = TRANS ? (t.gr < P.R) : (t.gr < P.B0);
+  t.valid_row = TRANS ? (t.gr < J.R) : (t.gr < J.B0);
+  t.in = (J.in_tab >= 0) ? (const void*)((const char*)P.ptrtab[J.in_tab] + J.tab_off_in) : J.in;
+  t.out = (J.out_tab >= 0) ? (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out) : J.out;
   return t;
 }
 
 template <bool IN_F64, bool TRANS>
-__device__ __forceinline__ void load_raw(const ModePass& P, const TileCtx& t, int c, int kq, Raw<IN_F64>& raw) {
-  const void* in = P.jobs[t.job].in;
-  const int n = P.n;
+__device__ __forceinline__ void load_raw(const TileCtx& t, int sub, int kq, Raw<IN_F64>& raw) {
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
-    const int k = c * KC + kq * 8 + e;
-    const bool ok = t.valid_row && k < n;
-    const long long idx = TRANS ? t.in_base + (long long)k * P.R + t.gr : t.gr * (long long)n + k;
+    const int k = sub * 32 + kq * 8 + e;
+    const bool ok = t.valid_row && k < t.n;
+    const long long idx = TRANS ? t.in_base + (long long)k * t.R + t.gr : t.gr * (long long)t.n + k;
     if (IN_F64)
-      raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(in) + idx) : 0.0;
+      raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(t.in) + idx) : 0.0;
     else
-      raw.f[e] = ok ? __ldg(reinterpret_cast<const float2*>(in) + idx) : make_float2(0.f, 0.f);
+      raw.f[e] = ok ? __ldg(reinterpret_cast<const float2*>(t.in) + idx) : make_float2(0.f, 0.f);
   }
 }
 
-template <int KS, bool IN_F64, bool TRANS>
-__global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant__ ModePass P, int* status) {
+// One tile = 128 operand rows (r for TRANS, X rows for NORMAL) x one 128-row half of E,
+// accumulated over the full contraction K = n in chunks of 32*SUB.
+template <int KS, int SUB, bool IN_F64, bool TRANS>
+__global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant__ GPass P, int* status) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  // [stage 0: X slices KS*8K | E slices KS*8K][stage 1: ...][mbarriers][column scales][tmem]
-  constexpr int STAGE_BYTES = 2 * KS * SLICE_BYTES;
+  // [stage 0: X slices SUB*KS*8K | E slices SUB*KS*8K][stage 1: ...][mbarriers][scales][tmem]
+  constexpr int HALF_BYTES = SUB * KS * SLICE_BYTES;
+  constexpr int STAGE_BYTES = 2 * HALF_BYTES;
   uint64_t* mbar_mma = reinterpret_cast<uint64_t*>(smem + 2 * STAGE_BYTES);   // 2: MMAs of stage done
   uint64_t* mbar_e = mbar_mma + 2;                                             // 2: E slices of stage landed
   float* scale_s = reinterpret_cast<float*>(smem + 2 * STAGE_BYTES + 64);     // 128 floats: 2^{eX + f_i}
@@ -307,13 +332,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int orow = tid & 127;   // operand row owned by this thread (r for TRANS, row for NORMAL)
-  const int kq = tid >> 7;      // which 8 of the chunk's 32 k this thread cuts
-  const int n = P.n;
-  const int nchunks = (n + KC - 1) / KC;
-  const long long R = P.R, B0 = P.B0;
-  const long long rtiles = TRANS ? (R + 127) / 128 : 1;
-  const long long tiles_per_job = TRANS ? B0 * rtiles : (B0 + 127) / 128;
-  const long long total_tiles = tiles_per_job * P.njobs;
+  const int kq = tid >> 7;      // which 8 of each 32-wide sub-chunk this thread cuts
+  const long long total_tiles = P.total_tiles;
 
   if (tid == 0) {
     for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_mma[q])));
@@ -328,7 +348,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_s;
-  const uint32_t idesc = TRANS ? make_idesc(128, n) : make_idesc(128, 128);
 
   uint32_t it = 0;          // global chunk counter (stage = it & 1, use = it >> 1)
   bool aborted = false;
@@ -336,17 +355,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
 
   long long tile = blockIdx.x;
   TileCtx T;
-  Raw<IN_F64> raw;
+  Raw<IN_F64> raw[SUB];
   if (tile < total_tiles) {
-    T = tile_ctx<TRANS>(P, tile, tiles_per_job, rtiles, orow);
-    load_raw<IN_F64, TRANS>(P, T, 0, kq, raw);
+    T = tile_ctx<TRANS>(P, tile, orow);
+#pragma unroll
+    for (int q = 0; q < SUB; ++q) load_raw<IN_F64, TRANS>(T, q, kq, raw[q]);
   }
   for (; tile < total_tiles && !aborted; tile += gridDim.x) {
-    const ModeJob& J = P.jobs[T.job];
+    const GJob& J = P.jobs[T.job];
+    const int n = T.n;
+    const int nchunks = (T.nsub + SUB - 1) / SUB;
+    const int nrows_e = min(128, n - 128 * T.half);   // E rows in this half
+    const uint8_t* ebase = J.eslices + (size_t)T.half * (size_t)T.nsub * KS * SLICE_BYTES;
     if (tid < 128) {
-      const int E = T.eX + ((tid < n) ? J.rexp[tid] : 0);
+      const int E = T.eX + ((tid < nrows_e) ? J.rexp[T.half * 128 + tid] : 0);
       scale_s[tid] = pow2f(E);
     }
+    const uint32_t idesc = TRANS ? make_idesc(128, nrows_e) : make_idesc(128, 128);
     const int eb = IN_F64 ? 1011 + T.eX : 86 + T.eX;
     bool init[4] = {false, false, false, false};
     TileCtx Tn = T;
@@ -354,50 +379,58 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
     for (int c = 0; c < nchunks; ++c, ++it) {
       const uint32_t st = it & 1u;
       uint8_t* sX = smem + st * STAGE_BYTES;
-      uint8_t* sE = sX + KS * SLICE_BYTES;
+      uint8_t* sE = sX + HALF_BYTES;
+      const int nsub_c = min(SUB, T.nsub - c * SUB);   // sub-chunks in this chunk
       int timed_out = fail;
       if (it >= 2) timed_out |= mbar_wait(smem_u32(&mbar_mma[st]), ((it >> 1) - 1) & 1u) ? 0 : 1;
       if (__syncthreads_or(timed_out)) {  // block-uniform decision
         aborted = true;
         break;
       }
-      if (tid == 0) {  // E slices of chunk c: one asynchronous bulk copy
-        const uint32_t bytes = (uint32_t)(KS * SLICE_BYTES);
+      if (tid == 0) {  // E slices of this chunk: one asynchronous bulk copy ([sub][slice][8 KB])
+        const uint32_t bytes = (uint32_t)(nsub_c * KS * SLICE_BYTES);
         mbar_expect_tx(smem_u32(&mbar_e[st]), bytes);
-        bulk_copy_g2s(smem_u32(sE), J.eslices + (size_t)c * KS * SLICE_BYTES, bytes, smem_u32(&mbar_e[st]));
+        bulk_copy_g2s(smem_u32(sE), ebase + (size_t)c * SUB * KS * SLICE_BYTES, bytes, smem_u32(&mbar_e[st]));
       }
       // raw values of the next chunk (or of the next tile's first chunk) go in flight now
-      Raw<IN_F64> rawn;
+      Raw<IN_F64> rawn[SUB];
       if (c + 1 < nchunks) {
-        load_raw<IN_F64, TRANS>(P, T, c + 1, kq, rawn);
+#pragma unroll
+        for (int q = 0; q < SUB; ++q)
+          if ((c + 1) * SUB + q < T.nsub) load_raw<IN_F64, TRANS>(T, (c + 1) * SUB + q, kq, rawn[q]);
       } else if (next_tile < total_tiles) {
-        Tn = tile_ctx<TRANS>(P, next_tile, tiles_per_job, rtiles, orow);
-        load_raw<IN_F64, TRANS>(P, Tn, 0, kq, rawn);
-      }
-      uint32_t pk[KS][4];
+        Tn = tile_ctx<TRANS>(P, next_tile, orow);
 #pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        uint32_t s0, s1;
-        uint64_t F0, F1;
-        if (IN_F64) {
-          F0 = fixed_f64(raw.d[e], eb, s0);
-          F1 = fixed_f64(raw.d[e + 1], eb, s1);
-        } else {
-          F0 = fixed_ff(raw.f[e].x, raw.f[e].y, eb, s0);
-          F1 = fixed_ff(raw.f[e + 1].x, raw.f[e + 1].y, eb, s1);
+        for (int q = 0; q < SUB; ++q)
+          if (q < Tn.nsub) load_raw<IN_F64, TRANS>(Tn, q, kq, rawn[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < SUB; ++q) {
+        if (q >= nsub_c) break;
+        uint32_t pk[KS][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          uint32_t s0, s1;
+          uint64_t F0, F1;
+          if (IN_F64) {
+            F0 = fixed_f64(raw[q].d[e], eb, s0);
+            F1 = fixed_f64(raw[q].d[e + 1], eb, s1);
+          } else {
+            F0 = fixed_ff(raw[q].f[e].x, raw[q].f[e].y, eb, s0);
+            F1 = fixed_ff(raw[q].f[e + 1].x, raw[q].f[e + 1].y, eb, s1);
+          }
+          F0 = round_digits<KS>(F0);
+          F1 = round_digits<KS>(F1);
+          uint32_t w[KS];
+          cut_pair<KS>(F0, s0, F1, s1, w);
+#pragma unroll
+          for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
         }
-        F0 = round_digits<KS>(F0);
-        F1 = round_digits<KS>(F1);
-        uint32_t w[KS];
-        cut_pair<KS>(F0, s0, F1, s1, w);
-#pragma unroll
-        for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
-      }
-      {
         const uint32_t off = (uint32_t)(orow >> 3) * 512u + (uint32_t)kq * 128u + (uint32_t)(orow & 7) * 16u;
 #pragma unroll
         for (int sl = 0; sl < KS; ++sl)
-          *reinterpret_cast<uint4*>(sX + sl * SLICE_BYTES + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+          *reinterpret_cast<uint4*>(sX + (q * KS + sl) * SLICE_BYTES + off) =
+              make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -407,24 +440,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
         } else {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t xa = smem_u32(sX), ea = smem_u32(sE);
+          for (int q = 0; q < nsub_c; ++q) {
 #pragma unroll
-          for (int s = 1; s <= KS; ++s) {          // E slice
+            for (int s = 1; s <= KS; ++s) {          // E slice
 #pragma unroll
-            for (int t = 1; t <= KS; ++t) {        // X slice
-              if (s + t > KS + 1) continue;
-              const int L = s + t - 2;
-              const int a = L < 3 ? L : 3;
-              const uint32_t dacc = tmem + (uint32_t)(a * 128);
+              for (int t = 1; t <= KS; ++t) {        // X slice
+                if (s + t > KS + 1) continue;
+                const int L = s + t - 2;
+                const int a = L < 3 ? L : 3;
+                const uint32_t dacc = tmem + (uint32_t)(a * 128);
 #pragma unroll
-              for (int ks = 0; ks < KC / 16; ++ks) {
-                const uint32_t xs = xa + (uint32_t)((t - 1) * SLICE_BYTES + ks * 256);
-                const uint32_t es = ea + (uint32_t)((s - 1) * SLICE_BYTES + ks * 256);
-                const uint64_t xd = make_desc(xs), ed = make_desc(es);
-                if (TRANS)
-                  mma_bf16(dacc, xd, ed, idesc, init[a] ? 1u : 0u);
-                else
-                  mma_bf16(dacc, ed, xd, idesc, init[a] ? 1u : 0u);
-                init[a] = true;
+                for (int ks = 0; ks < 2; ++ks) {
+                  const uint32_t xs = xa + (uint32_t)((q * KS + t - 1) * SLICE_BYTES + ks * 256);
+                  const uint32_t es = ea + (uint32_t)((q * KS + s - 1) * SLICE_BYTES + ks * 256);
+                  const uint64_t xd = make_desc(xs), ed = make_desc(es);
+                  if (TRANS)
+                    mma_bf16(dacc, xd, ed, idesc, init[a] ? 1u : 0u);
+                  else
+                    mma_bf16(dacc, ed, xd, idesc, init[a] ? 1u : 0u);
+                  init[a] = true;
+                }
               }
             }
           }
@@ -433,7 +468,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a) init[a] = true;
-      raw = rawn;
+#pragma unroll
+      for (int q = 0; q < SUB; ++q) raw[q] = rawn[q];
     }
     if (aborted) break;
     // epilogue: wait for the last chunk's MMAs (covers every earlier MMA of this tile)
@@ -449,13 +485,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
       const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
       const int lrow = (warp & 3) * 32 + lane;  // TMEM lane of this thread
       const int cq = warp >> 2;
-      int emax = -1000;
-      const int ncols = TRANS ? ((n + 15) & ~15) : 128;
+      int emax = 0;
+      const int ncols = TRANS ? ((nrows_e + 15) & ~15) : 128;
       const int ngroups = ncols / 16;
       const int gbeg = (cq * ngroups) / 4, gend = ((cq + 1) * ngroups) / 4;
-      float2* outFF = reinterpret_cast<float2*>(J.out);
-      double* outF64 = reinterpret_cast<double*>(J.out);
-      const long long out_base = TRANS ? T.b0 * (long long)n * R : 0;
+      float2* outFF = reinterpret_cast<float2*>(T.out);
+      double* outF64 = reinterpret_cast<double*>(T.out);
+      const long long out_base = TRANS ? T.b0 * (long long)n * T.R : 0;
       const float lane_scale = TRANS ? 1.0f : scale_s[lrow];
       for (int gq = gbeg; gq < gend; ++gq) {
         const int cc = gq * 16;
@@ -468,20 +504,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int col = cc + j;
-          int i;
+          int il, i;
           long long oidx;
           bool ok;
           float sc;
           if (TRANS) {
-            i = col;
+            il = col;
+            i = 128 * T.half + il;
             const long long g = T.r0 + lrow;
-            ok = (i < n) && (g < R);
-            oidx = out_base + (long long)i * R + g;
-            sc = scale_s[i];
+            ok = (il < nrows_e) && (g < T.R);
+            oidx = out_base + (long long)i * T.R + g;
+            sc = scale_s[il];
           } else {
-            i = lrow;
+            il = lrow;
+            i = 128 * T.half + il;
             const long long g = T.row0 + col;
-            ok = (i < n) && (g < B0);
+            ok = (il < nrows_e) && (g < T.B0);
             oidx = g * (long long)n + i;
             sc = lane_scale;
           }
@@ -525,15 +563,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-template <int KS>
-size_t smem_bytes() {
-  return (size_t)2 * 2 * KS * SLICE_BYTES + 64 + 512 + 16 + 16;
+__global__ void ptrtab_set_kernel(void** tab, PtrArgs args) {
+  const int i = threadIdx.x;
+  if (i < args.n) tab[i] = args.p[i];
 }
 
-template <int KS, bool IN_F64, bool TRANS>
-int launch_one(const ModePass& P, int* status, int nsm, cudaStream_t st) {
-  const size_t sm = smem_bytes<KS>();
-  auto kern = mode_kernel<KS, IN_F64, TRANS>;
+}  // namespace
+
+size_t smem_bytes(int ks, int sub) {
+  return (size_t)2 * 2 * sub * ks * SLICE_BYTES + 64 + 512 + 16 + 16;
+}
+
+template <int KS, int SUB, bool IN_F64, bool TRANS>
+int launch_one(const GPass& P, int grid, int* status, cudaStream_t st) {
+  const size_t sm = smem_bytes(KS, SUB);
+  auto kern = mode_kernel<KS, SUB, IN_F64, TRANS>;
   static bool attr = false;  // per instantiation
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -543,10 +587,6 @@ int launch_one(const ModePass& P, int* status, int nsm, cudaStream_t st) {
     }
     attr = true;
   }
-  const long long rtiles = TRANS ? (P.R + 127) / 128 : 1;
-  const long long tiles = (TRANS ? P.B0 * rtiles : (P.B0 + 127) / 128) * P.njobs;
-  const int grid = (int)(tiles < nsm ? tiles : nsm);
-  if (grid <= 0) return PHIKRON_OK;
   launch_begin(KC_TC_MODE, st);
   kern<<<grid, NTHREADS, sm, st>>>(P, status);
   launch_end(st);
@@ -554,30 +594,37 @@ int launch_one(const ModePass& P, int* status, int nsm, cudaStream_t st) {
   return PHIKRON_OK;
 }
 
-template <int KS>
-int launch_ks(const ModePass& P, int* status, int nsm, cudaStream_t st) {
-  const bool trans = P.R > 1;
-  if (P.in_f64) {
-    return trans ? launch_one<KS, true, true>(P, status, nsm, st) : launch_one<KS, true, false>(P, status, nsm, st);
-  }
-  return trans ? launch_one<KS, false, true>(P, status, nsm, st) : launch_one<KS, false, false>(P, status, nsm, st);
+template <int KS, int SUB>
+int launch_ks(const GPass& P, bool in_f64, bool trans, int grid, int* status, cudaStream_t st) {
+  if (in_f64)
+    return trans ? launch_one<KS, SUB, true, true>(P, grid, status, st) : launch_one<KS, SUB, true, false>(P, grid, status, st);
+  return trans ? launch_one<KS, SUB, false, true>(P, grid, status, st) : launch_one<KS, SUB, false, false>(P, grid, status, st);
 }
 
-int mode_pass(const ModePass& P, int ks, int* status, int nsm, cudaStream_t st) {
-  if (P.njobs <= 0) return PHIKRON_OK;
-  if (P.n < 16 || P.n > 128 || (P.n % 16) != 0) {
-    set_error("tc mode pass: n must be a multiple of 16 in 16..128");
-    return PHIKRON_ENOTSUP;
+int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) {
+  if (P.njobs <= 0 || P.total_tiles <= 0) return PHIKRON_OK;
+  const int grid = (int)std::min<long long>(P.total_tiles, S.grid);
+  if (S.sub == 1) {
+    switch (S.slices) {
+      case 3: return launch_ks<3, 1>(P, S.in_f64, S.trans, grid, status, st);
+      case 4: return launch_ks<4, 1>(P, S.in_f64, S.trans, grid, status, st);
+      case 5: return launch_ks<5, 1>(P, S.in_f64, S.trans, grid, status, st);
+      case 6: return launch_ks<6, 1>(P, S.in_f64, S.trans, grid, status, st);
+      default: break;
+    }
+  } else if (S.sub == 2 && S.slices == 3) {
+    return launch_ks<3, 2>(P, S.in_f64, S.trans, grid, status, st);
   }
-  switch (ks) {
-    case 3: return launch_ks<3>(P, status, nsm, st);
-    case 4: return launch_ks<4>(P, status, nsm, st);
-    case 5: return launch_ks<5>(P, status, nsm, st);
-    case 6: return launch_ks<6>(P, status, nsm, st);
-    default:
-      set_error("tc mode pass: slices must be 3..6");
-      return PHIKRON_EINVAL;
-  }
+  set_error("tc mode pass: unsupported (slices, sub-chunks) combination");
+  return PHIKRON_EINVAL;
+}
+
+int set_ptrtab(void** tab, const PtrArgs& args, cudaStream_t st) {
+  launch_begin(KC_OTHER, st);
+  ptrtab_set_kernel<<<1, 128, 0, st>>>(tab, args);
+  launch_end(st);
+  PK_CHECK_LAUNCH();
+  return PHIKRON_OK;
 }
 
 }  // namespace tc

@@ -33,7 +33,8 @@ class PhikronError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("quad", C.c_int), ("precision", C.c_int), ("selector", C.c_int),
                 ("force_s", C.c_int), ("force_m", C.c_int), ("alpha", C.c_double),
-                ("beta", C.c_double), ("device", C.c_int), ("max_rhs", C.c_int), ("slices", C.c_int)]
+                ("beta", C.c_double), ("device", C.c_int), ("max_rhs", C.c_int), ("slices", C.c_int),
+                ("half_step", C.c_int)]
 
 
 class Info(C.Structure):
@@ -49,6 +50,12 @@ class Profile(C.Structure):
 
 
 KERNEL_CLASSES = ("gemm_f64", "weighted_sum", "squaring", "tc_mode", "convert", "other")
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("units", C.c_int), ("launches", C.c_int), ("mode_jobs", C.c_longlong), ("graph", C.c_int),
+                ("k_chunk", C.c_int), ("big_first", C.c_int), ("grid", C.c_int), ("candidates", C.c_int),
+                ("tuned", C.c_int), ("best_ms", C.c_double), ("device_bytes", C.c_size_t)]
 
 _lib = None
 
@@ -68,6 +75,12 @@ SIGNATURES = {
     "phikron_destroy": (None, [C.c_void_p]),
     "phikron_check_status": (C.c_int, [C.c_void_p]),
     "phikron_last_error": (C.c_char_p, []),
+    "phikron_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p), C.c_int,
+                                       C.c_int, C.c_int]),
+    "phikron_batch_apply": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
+    "phikron_batch_get_info": (C.c_int, [C.c_void_p, C.POINTER(BatchInfo)]),
+    "phikron_batch_check_status": (C.c_int, [C.c_void_p]),
+    "phikron_batch_destroy": (None, [C.c_void_p]),
     "phikron_profile_begin": (C.c_int, [C.c_void_p, C.c_int]),
     "phikron_profile_end": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "phikron_log_quaderr": (C.c_int, [C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _DP]),
@@ -158,7 +171,8 @@ class Plan:
 
     def __init__(self, factors, tau: float, l_max: int, tol: float, *, precision: int = PREC_FP64,
                  quad: int = QUAD_GAUSS, force_s: int = -1, force_m: int = -1, alpha: float = 0.0,
-                 beta: float = 0.0, device: int = -1, max_rhs: int = 1, slices: int = 0):
+                 beta: float = 0.0, device: int = -1, max_rhs: int = 1, slices: int = 0,
+                 half_step: bool = False):
         L = lib()
         self._h = C.c_void_p()
         facs = [np.ascontiguousarray(a, dtype=np.float64) for a in factors]
@@ -172,11 +186,13 @@ class Plan:
         L.phikron_opts_default(C.byref(o))
         o.quad, o.precision, o.force_s, o.force_m = quad, precision, force_s, force_m
         o.alpha, o.beta, o.device, o.max_rhs, o.slices = alpha, beta, device, max_rhs, slices
+        o.half_step = 1 if half_step else 0
         _check(L.phikron_plan(C.byref(self._h), len(facs), ptrs, ns, tau, l_max, tol, C.byref(o)))
         self.shape = tuple(a.shape[0] for a in facs)
         self.N = int(np.prod(self.shape))
         self.l_max = l_max
         self.max_rhs = max_rhs
+        self.nout = (l_max + 1) * (2 if half_step else 1)
 
     def info(self) -> dict:
         inf = Info()
@@ -195,7 +211,7 @@ class Plan:
         if V.dtype != torch.float64 or not V.is_cuda or not V.is_contiguous() or V.numel() != self.N:
             raise ValueError("V must be a contiguous CUDA float64 tensor with N entries")
         if Out is None:
-            Out = torch.empty((self.l_max + 1, self.N), dtype=torch.float64, device=V.device)
+            Out = torch.empty((self.nout, self.N), dtype=torch.float64, device=V.device)
         _check(lib().phikron_apply(self._h, V.data_ptr(), Out.data_ptr(), _stream_ptr(stream)))
         return Out
 
@@ -204,7 +220,7 @@ class Plan:
         import torch
         nrhs = V.shape[0]
         if Out is None:
-            Out = torch.empty((nrhs, self.l_max + 1, self.N), dtype=torch.float64, device=V.device)
+            Out = torch.empty((nrhs, self.nout, self.N), dtype=torch.float64, device=V.device)
         _check(lib().phikron_apply_many(self._h, nrhs, V.data_ptr(), Out.data_ptr(), _stream_ptr(stream)))
         return Out
 
@@ -212,7 +228,7 @@ class Plan:
         """Host-memory apply (copies in, applies, copies out; synchronous)."""
         v = np.ascontiguousarray(v, dtype=np.float64).ravel()
         if out is None:
-            out = np.empty((self.l_max + 1, self.N))
+            out = np.empty((self.nout, self.N))
         st = 0 if stream is None else _stream_ptr(stream)
         _check(lib().phikron_apply_host(self._h, _dp(v), _dp(out), C.c_void_p(st)))
         return out
@@ -241,6 +257,49 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib().phikron_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """phikron_batch_t owner: plans x nrhs right-hand sides in grouped launches (one graph)."""
+
+    def __init__(self, plans, nrhs: int = 1, half_step: bool = False, autotune: bool = False):
+        self._plans = list(plans)
+        self._h = C.c_void_p()
+        arr = (C.c_void_p * len(self._plans))(*[p._h.value for p in self._plans])
+        _check(lib().phikron_batch_create(C.byref(self._h), len(self._plans), arr, nrhs,
+                                          1 if half_step else 0, 1 if autotune else 0))
+        self.nrhs = nrhs
+        self.half_step = half_step
+
+    def apply(self, V, Out=None, stream=None):
+        """V: list of CUDA float64 tensors (nrhs, N_i); returns list of (nrhs, nout, N_i)."""
+        import torch
+        if Out is None:
+            Out = [torch.empty((self.nrhs, p.nout, p.N), dtype=torch.float64, device=v.device)
+                   for p, v in zip(self._plans, V)]
+        vp = (C.c_void_p * len(V))(*[v.data_ptr() for v in V])
+        op = (C.c_void_p * len(Out))(*[o.data_ptr() for o in Out])
+        _check(lib().phikron_batch_apply(self._h, vp, op, _stream_ptr(stream)))
+        return Out
+
+    def info(self) -> dict:
+        inf = BatchInfo()
+        _check(lib().phikron_batch_get_info(self._h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in BatchInfo._fields_}
+
+    def check_status(self):
+        _check(lib().phikron_batch_check_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().phikron_batch_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

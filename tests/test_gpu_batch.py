@@ -1,0 +1,108 @@
+"""GPU parity of the batched apply (grouped persistent launches over uneven instances x
+right-hand sides, one CUDA graph) and of the pieces it needs: sizes above 128 (E split into
+row halves), and the half-step outputs phi_l(-tau/2 A) v.
+
+Oracle: the spectral definition O2 (sine transform), exact for these symmetric Dirichlet
+diffusion operators at any size.  Bounds: for a mode with n > 128 the second digit level
+rounds at ~2^-32 of a product, so plans touching such a mode are held to 5e-8 (slices >= 4);
+the quadrature tolerance adds tol.  A batched result must equal the same plan's single apply
+bit for bit (every tile computes the same operations; only scheduling differs).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import phi as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _pk():
+    import paper_2211_00696_gb300 as pk
+    return pk
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _diffusion(shape, coeff):
+    return [W.laplacian_factor(n, coeff) for n in shape]
+
+
+@pytest.mark.parametrize("shape", [(192, 16, 32), (32, 256, 16), (16, 48, 256), (160, 144)])
+def test_sizes_above_128_vs_spectral(shape):
+    pk = _pk()
+    coeff, tau = 0.3, 2e-5
+    fac = _diffusion(shape, coeff)
+    v = W.uniform_vector(shape, 9)
+    plan = pk.Plan(fac, tau, 3, 1e-9, precision=pk.PREC_OZAKI_BF16, slices=5)
+    out = plan.apply(_dev(v)).cpu().numpy()
+    plan.check_status()
+    exact = P.phi_spectral_dirichlet(shape, [coeff] * len(shape), tau, v, 3)
+    for l in range(4):
+        assert P.rel_err_2(out[l], exact[l]) <= 5e-8, (shape, l, P.rel_err_2(out[l], exact[l]))
+
+
+def test_half_step_outputs_vs_spectral():
+    pk = _pk()
+    shape, coeff, tau = (48, 64, 32), 0.5, 1e-3
+    fac = _diffusion(shape, coeff)
+    v = W.uniform_vector(shape, 10)
+    plan = pk.Plan(fac, tau, 3, 1e-10, precision=pk.PREC_OZAKI_BF16, slices=5, half_step=True)
+    assert plan.info()["s"] >= 1
+    out = plan.apply(_dev(v)).cpu().numpy()
+    plan.check_status()
+    full = P.phi_spectral_dirichlet(shape, [coeff] * 3, tau, v, 3)
+    half = P.phi_spectral_dirichlet(shape, [coeff] * 3, tau / 2, v, 3)
+    for l in range(4):
+        assert P.rel_err_2(out[l], full[l]) <= 1e-9, l
+        assert P.rel_err_2(out[4 + l], half[l]) <= 1e-9, l
+    # a tiny tau plans s = 0; half_step forces s = 1
+    plan = pk.Plan(fac, 1e-7, 2, 1e-10, precision=pk.PREC_OZAKI_BF16, slices=5, half_step=True)
+    assert plan.info()["s"] == 1
+    out = plan.apply(_dev(v)).cpu().numpy()
+    half = P.phi_spectral_dirichlet(shape, [coeff] * 3, 0.5e-7, v, 2)
+    for l in range(3):
+        assert P.rel_err_2(out[3 + l], half[l]) <= 1e-9, l
+
+
+def _instances(seed, count, sizes):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        shape = tuple(int(s) for s in rng.choice(sizes, size=3))
+        out.append(dict(shape=shape, coeff=float(rng.uniform(0.1, 1.0)),
+                        tau=float(10.0 ** rng.uniform(-6.0, -3.0))))
+    return out
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batched_uneven_matches_single_and_spectral(autotune):
+    pk = _pk()
+    insts = _instances(31, 6, (16, 32, 48, 64, 96, 160))
+    nrhs, p = 2, 3
+    plans = [pk.Plan(_diffusion(d["shape"], d["coeff"]), d["tau"], p, 1e-8, precision=pk.PREC_OZAKI_BF16,
+                     slices=4, half_step=True) for d in insts]
+    batch = pk.Batch(plans, nrhs=nrhs, half_step=True, autotune=autotune)
+    V = [np.stack([W.uniform_vector(d["shape"], 200 + 10 * i + r) for r in range(nrhs)])
+         for i, d in enumerate(insts)]
+    Vd = [_dev(x) for x in V]
+    out = [o.cpu().numpy() for o in batch.apply(Vd)]
+    out2 = [o.cpu().numpy() for o in batch.apply(Vd)]    # second call (tuned shape, graph replay)
+    batch.check_status()
+    info = batch.info()
+    assert info["units"] == len(insts) * nrhs and info["graph"] == 1 and info["tuned"] == 1
+    if autotune:
+        assert info["candidates"] >= 2
+    for i, d in enumerate(insts):
+        assert np.array_equal(out[i], out2[i])
+        for r in range(nrhs):
+            single = plans[i].apply(Vd[i][r]).cpu().numpy()
+            assert np.array_equal(out[i][r], single), (i, r)
+            full = P.phi_spectral_dirichlet(d["shape"], [d["coeff"]] * 3, d["tau"], V[i][r], p)
+            half = P.phi_spectral_dirichlet(d["shape"], [d["coeff"]] * 3, d["tau"] / 2, V[i][r], p)
+            for l in range(p + 1):
+                assert P.rel_err_2(out[i][r][l], full[l]) <= 5e-8, (i, r, l)
+                assert P.rel_err_2(out[i][r][p + 1 + l], half[l]) <= 5e-8, (i, r, l)
