@@ -201,6 +201,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """Uneven batched workload: 32 3D diffusion instances with sizes from {64,...,256},
+    4 right-hand sides, phi_0..phi_3 at tau and tau/2, 3 digit slices; one grouped graph per
+    apply.  value = unknowns (instances x RHS x N_i) per second."""
+    import torch
+    import paper_2211_00696_gb300 as pk
+    torch.cuda.set_device(0)
+    insts = W.batched_uneven3d()
+    t0 = time.perf_counter()
+    plans = [pk.Plan(W.batched_instance_factors(d), d["tau"], 3, 1e-6, precision=pk.PREC_OZAKI_BF16,
+                     slices=3, half_step=True) for d in insts]
+    batch = pk.Batch(plans, nrhs=4, half_step=True, autotune=True)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    V = [torch.stack([torch.from_numpy(W.uniform_vector(d["shape"], s)) for s in d["rhs_seeds"]]).cuda()
+         for d in insts]
+    out = batch.apply(V)            # autotunes on this first call
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        batch.apply(V, out)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        batch.apply(V, out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    unknowns = 4 * sum(int(np.prod(d["shape"])) for d in insts)
+    info = batch.info()
+    print(json.dumps({"metric": "batched phi_0..3 at tau and tau/2, unknowns/s", "value": unknowns / (ms * 1e-3),
+                      "unit": UNIT, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                      "unknowns_per_step": unknowns, "plan_and_batch_ms": plan_ms,
+                      "config": {"workload": "batched_uneven3d_32x4rhs", "slices": 3,
+                                 "s": [p.info()["s"] for p in plans], "m": [p.info()["m"] for p in plans]},
+                      "batch": info}), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -344,11 +382,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--workload", default="convdiff3d", choices=["convdiff3d", "batched"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -170,7 +170,9 @@ int phikron_check_status(phikron_plan_t plan);
  * and l_max, on one device; at most 64 plans.  The plans must outlive the batch.
  *
  * phikron_batch_create: allocates the batch's work buffers (device memory ~ 8 bytes x
- *   nrhs x sum_i (2 (m_i+2) + 2 l_max) N_i).  half_step != 0 also returns phi_l at tau/2
+ *   (nrhs-1) x sum_i (2 (m_i+2) + 2 l_max) N_i; the first right-hand side uses each plan's
+ *   own buffers, so a batch and a single apply of one of its plans must not overlap on the
+ *   GPU).  half_step != 0 also returns phi_l at tau/2
  *   (plans made with opts.half_step).  autotune != 0: the first apply times the candidate
  *   launch shapes (K chunk 32/64, job order, grid) and keeps the fastest.
  * phikron_batch_apply: V[i] (DEVICE) holds nrhs vectors of plan i (rhs r at V[i] + r*N_i);

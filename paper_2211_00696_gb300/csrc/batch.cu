@@ -123,10 +123,17 @@ int phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* 
         u.inst = i;
         u.rhs = r;
         void *w1, *w2, *y, *yn;
-        if ((rc = walloc(*B, &w1, sizeof(float2) * (size_t)nv * P.N)) != PHIKRON_OK) break;
-        if ((rc = walloc(*B, &w2, sizeof(float2) * (size_t)nv * P.N)) != PHIKRON_OK) break;
-        if ((rc = walloc(*B, &y, sizeof(float2) * (size_t)std::max(P.p, 1) * P.N)) != PHIKRON_OK) break;
-        if ((rc = walloc(*B, &yn, sizeof(float2) * (size_t)std::max(P.p, 1) * P.N)) != PHIKRON_OK) break;
+        if (r == 0) {  // the first right-hand side reuses the plan's own work buffers
+          w1 = P.dW1;
+          w2 = P.dW2;
+          y = P.dY;
+          yn = P.dYn;
+        } else {
+          if ((rc = walloc(*B, &w1, sizeof(float2) * (size_t)nv * P.N)) != PHIKRON_OK) break;
+          if ((rc = walloc(*B, &w2, sizeof(float2) * (size_t)nv * P.N)) != PHIKRON_OK) break;
+          if ((rc = walloc(*B, &y, sizeof(float2) * (size_t)std::max(P.p, 1) * P.N)) != PHIKRON_OK) break;
+          if ((rc = walloc(*B, &yn, sizeof(float2) * (size_t)std::max(P.p, 1) * P.N)) != PHIKRON_OK) break;
+        }
         u.W1 = (float2*)w1;
         u.W2 = (float2*)w2;
         u.Y = (float2*)y;

@@ -106,3 +106,41 @@ def test_batched_uneven_matches_single_and_spectral(autotune):
             for l in range(p + 1):
                 assert P.rel_err_2(out[i][r][l], full[l]) <= 5e-8, (i, r, l)
                 assert P.rel_err_2(out[i][r][p + 1 + l], half[l]) <= 5e-8, (i, r, l)
+
+
+def test_config3_full_size_batched():
+    """32 instances, (n_x, n_y, n_z) from {64, 96, 128, 192, 256}, c ~ U(0.1, 1),
+    tau ~ logU(1e-4, 1e-1), 4 right-hand sides, phi_0..phi_3 at tau and tau/2, FP32-class
+    digit products (3 slices) with float64 exponentials; autotuned grouped launches in one
+    graph.  Checked: the smallest, a middle and the largest instance against the spectral
+    oracle (all 4 RHS x 8 outputs of the smallest, RHS 0 of the others), and every output
+    finite."""
+    pk = _pk()
+    insts = W.batched_uneven3d()
+    N = [int(np.prod(d["shape"])) for d in insts]
+    need = 8.0 * 4 * sum(N) * (2 * 12 + 2 * 3 + 1 + 8) * 1.15
+    free, _ = torch.cuda.mem_get_info()
+    if free < need:
+        pytest.skip(f"needs ~{need / 2**30:.0f} GiB of device memory, {free / 2**30:.0f} GiB free")
+    plans = [pk.Plan(W.batched_instance_factors(d), d["tau"], 3, 1e-6, precision=pk.PREC_OZAKI_BF16,
+                     slices=3, half_step=True) for d in insts]
+    batch = pk.Batch(plans, nrhs=4, half_step=True, autotune=True)
+    V = [torch.stack([torch.from_numpy(W.uniform_vector(d["shape"], s)) for s in d["rhs_seeds"]]).cuda()
+         for d in insts]
+    out = batch.apply(V)
+    batch.check_status()
+    assert batch.info()["tuned"] == 1
+    for o in out:
+        assert bool(torch.isfinite(o).all())
+    order = np.argsort(N)
+    for rank, i in enumerate([order[0], order[len(order) // 2], order[-1]]):
+        d = insts[i]
+        rhs_list = range(4) if rank == 0 else [0]
+        for r in rhs_list:
+            v = V[i][r].cpu().numpy()
+            got = out[i][r].cpu().numpy()
+            full = P.phi_spectral_dirichlet(d["shape"], [d["coeff"]] * 3, d["tau"], v, 3)
+            half = P.phi_spectral_dirichlet(d["shape"], [d["coeff"]] * 3, d["tau"] / 2, v, 3)
+            for l in range(4):
+                assert P.rel_err_2(got[l], full[l]) <= 2e-5, (i, r, l)
+                assert P.rel_err_2(got[4 + l], half[l]) <= 2e-5, (i, r, l)
