@@ -57,8 +57,8 @@ extern "C" {
                                          rounds at ~2^-32 relative (FP32-class products).   */
 
 #define PHIKRON_SELECT_PAPER      0   /* (s, m) from Algorithm 5                            */
-#define PHIKRON_SELECT_MLP        1   /* (s, m) from the learned selector, Algorithm 5 as
-                                         fallback (see phikron_selector_*)                  */
+#define PHIKRON_SELECT_MLP        1   /* (s, m) from the learned selector, checked a posteriori,
+                                         Algorithm 5 as fallback (see phikron_selector_*)   */
 
 typedef struct phikron_opts {
   int    quad;        /* PHIKRON_QUAD_*; default GAUSS                                        */
@@ -144,7 +144,8 @@ typedef struct phikron_info {
   int    actions;      /* Kronecker actions per apply: m + s*l_max + 1 (phi_0)          */
   double alpha;        /* ||tau*A||_inf estimate used                                   */
   double log10_bound;  /* log10 of Algorithm 3's bound at the chosen (s, m)             */
-  int    precision, quad, selector_used;
+  int    precision, quad;
+  int    selector_used;  /* 0 Algorithm 5, 1 network, 2 network (m raised), 3 fallback         */
   int    unique_factors;
   size_t device_bytes; /* device memory held by the plan                                */
   int    slices;       /* digit slices of the mixed path (0 for FP64)                   */
@@ -202,6 +203,43 @@ int  phikron_batch_apply(phikron_batch_t batch, const double* const* V, double* 
 int  phikron_batch_get_info(phikron_batch_t batch, phikron_batch_info* info);
 int  phikron_batch_check_status(phikron_batch_t batch);
 void phikron_batch_destroy(phikron_batch_t batch);
+
+/* ------------------------------------------------------------------ learned (s, m) selector
+ * A small FP32 network 8 -> 64 -> 64 -> (21 + 31) (ReLU) predicts the scaling s (0..20) and
+ * the node count m (2..32) from 8 cheap features (phikron_selector_features).  Plans made
+ * with opts.selector = PHIKRON_SELECT_MLP run it on the GPU, then check the prediction a
+ * posteriori with the measured criterion below over the Gershgorin interval of -tau*A
+ * (symmetric factors only), raise m by up to 4 if needed, and otherwise fall back to
+ * Algorithm 5 (phikron_info.selector_used: 0 Algorithm 5, 1 network, 2 network with raised
+ * m, 3 network rejected -> Algorithm 5).  The tolerance of the check is a 2-norm error
+ * relative to ||v||_2 (for symmetric A the criterion bounds it).
+ *
+ * Measured criterion: for the scalar method at z (Gauss-Legendre quadrature of Eq. (3) at
+ * 2^-s z, then s scalar squaring steps of Eq. (29)) the largest |Phi_j(z) - phi_j(z)|,
+ * j = 1..p, over npts Chebyshev-spaced points of [zlo, zhi] (zlo <= zhi <= 0).
+ * Search (training labels): the (s, m) minimising m + s*p subject to criterion <= tol, in
+ * Algorithm 5's shape.  Model parameters are a flat FP32 array of
+ * phikron_selector_param_count() floats ([W1 8x64][b1][W2 64x64][b2][W3 64x52][b3], row-major
+ * in x out); the model is process-wide.
+ */
+int  phikron_selector_features(int dims, const int* n, const double* tau_norm_inf, int l_max, double tol,
+                               float* out8);   /* log10(tau||A^d||inf), log2(n_d)/8, l_max/4, -log10(tol)/10 */
+int  phikron_selector_criterion(double zlo, double zhi, int p, int s, int m, int npts, double* err);
+int  phikron_selector_search(int count, const double* zlo, const double* zhi, const int* p, const double* tol,
+                             int npts, int nthreads, int* s, int* m, int* cost);   /* HOST arrays */
+int  phikron_selector_param_count(void);
+int  phikron_selector_set_model(const float* params, int n);   /* HOST */
+int  phikron_selector_get_model(float* params, int n);         /* HOST */
+/* DEVICE arrays: params (param_count), X (count x 8); logits (count x 52), s, m may be NULL */
+int  phikron_selector_forward(const float* params, const float* X, int count, float* logits, int* s, int* m,
+                              void* stream);
+/* DEVICE arrays: gradient of the mean loss (cross-entropy on both heads) over count samples */
+int  phikron_selector_grad(const float* params, const float* X, const int* ys, const int* ym, int count,
+                           float* grad, float* loss, void* stream);
+/* HOST arrays; trains with Adam on the GPU (hand-written kernels), synchronous; the result
+ * becomes the process-wide model.  init may be NULL (He initialisation from seed). */
+int  phikron_selector_train(const float* X, const int* ys, const int* ym, int count, int epochs, int batch,
+                            float lr, unsigned seed, const float* init, float* params_out, float* final_loss);
 
 /* ------------------------------------------------------------------ per-kernel timing
  * Between phikron_profile_begin and phikron_profile_end every kernel the plan's applies

@@ -88,6 +88,86 @@ int Plan::alloc(void** p, size_t bytes) {
   return PHIKRON_OK;
 }
 
+void selector_features(int dims, const int* n, const double* tau_norm_inf, int p, double tol, float* out) {
+  for (int d = 0; d < 3; ++d) {
+    if (d < dims) {
+      out[d] = (float)std::log10(std::max(tau_norm_inf[d], 1e-30));
+      out[3 + d] = (float)(std::log2((double)n[d]) / 8.0);
+    } else {
+      out[d] = -6.0f;
+      out[3 + d] = 0.0f;
+    }
+  }
+  out[6] = (float)(p / 4.0);
+  out[7] = (float)(-std::log10(tol) / 10.0);
+}
+
+namespace {
+
+bool is_symmetric(const double* a, int n) {
+  double mx = 0.0;
+  for (long long i = 0; i < (long long)n * n; ++i) mx = std::max(mx, std::fabs(a[i]));
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (std::fabs(a[(size_t)i * n + j] - a[(size_t)j * n + i]) > 1e-14 * mx) return false;
+  return true;
+}
+
+// (s, m) from the learned selector with an a-posteriori check of the measured criterion over
+// the Gershgorin interval of M = -tau*A; returns 1 (network), 2 (network, m raised until the
+// check passes) or 3 (check failed: caller falls back to Algorithm 5).
+int select_mlp(int dims, const double* const* A, const int* n, double tau, int l_max, double tol, int* s, int* m) {
+  std::vector<float> params;
+  if (!mlp::model(&params)) return -1;
+  double tn[3] = {0, 0, 0}, glo = 0.0, ghi = 0.0;
+  bool sym = true;
+  for (int d = 0; d < dims; ++d) {
+    tn[d] = std::fabs(tau) * norm_inf(A[d], n[d]);
+    sym = sym && is_symmetric(A[d], n[d]);
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < n[d]; ++i) {
+      double r = 0.0;
+      for (int j = 0; j < n[d]; ++j)
+        if (j != i) r += std::fabs(A[d][(size_t)i * n[d] + j]);
+      lo = std::min(lo, A[d][(size_t)i * n[d] + i] - r);
+      hi = std::max(hi, A[d][(size_t)i * n[d] + i] + r);
+    }
+    glo += lo;
+    ghi += hi;
+  }
+  float feat[8];
+  selector_features(dims, n, tn, l_max, tol, feat);
+  float *dp = nullptr, *dx = nullptr;
+  int* dsm = nullptr;
+  int hs = 0, hm = 0;
+  bool ok = cudaMalloc(&dp, sizeof(float) * params.size()) == cudaSuccess &&
+            cudaMalloc(&dx, sizeof(float) * 8) == cudaSuccess && cudaMalloc(&dsm, sizeof(int) * 2) == cudaSuccess;
+  ok = ok && cudaMemcpy(dp, params.data(), sizeof(float) * params.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(dx, feat, sizeof(float) * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && mlp::forward(dp, dx, 1, nullptr, dsm, dsm + 1, nullptr) == PHIKRON_OK;
+  ok = ok && cudaMemcpy(&hs, dsm, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+  ok = ok && cudaMemcpy(&hm, dsm + 1, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaFree(dp);
+  cudaFree(dx);
+  cudaFree(dsm);
+  if (!ok) {
+    cudaGetLastError();
+    return 3;
+  }
+  const double zlo = -std::fabs(tau) * ghi, zhi = -std::fabs(tau) * glo;
+  if (!sym || zhi > 0.0 || !(zlo <= zhi)) return 3;  // outside the criterion's reach
+  for (int extra = 0; extra <= 4 && hm + extra <= 32; ++extra) {
+    if (selector::criterion(zlo, zhi, l_max, hs, hm + extra, 512) <= tol) {
+      *s = hs;
+      *m = hm + extra;
+      return extra == 0 ? 1 : 2;
+    }
+  }
+  return 3;
+}
+
+}  // namespace
+
 // ----------------------------------------------------------------------------- plan
 
 int build_plan(Plan& P, int dims, const double* const* A, const int* n, double tau, int l_max,
@@ -118,8 +198,21 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
 
   // (s, m): Algorithm 5, unless forced or trivial
   int s = 0, m = 0, cost = 0;
+  P.selector_used = PHIKRON_SELECT_PAPER;
   if (l_max >= 1) {
-    if (alpha > 0.0) {
+    int sel = 0;
+    if (o.selector == PHIKRON_SELECT_MLP && alpha > 0.0 && o.quad == PHIKRON_QUAD_GAUSS) {
+      sel = select_mlp(dims, A, n, tau, l_max, tol, &s, &m);
+      if (sel < 0) {
+        set_error("phikron_plan: PHIKRON_SELECT_MLP needs a selector model (phikron_selector_set_model or "
+                  "phikron_selector_train)");
+        return PHIKRON_EINVAL;
+      }
+      P.selector_used = (sel == 3) ? 3 : sel;
+    }
+    if (sel == 1 || sel == 2) {
+      // (s, m) from the network, checked
+    } else if (alpha > 0.0) {
       PK_RET(planner::setup_quadrature(tol, l_max, alpha, beta, o.quad, &s, &m, &cost));
     } else {
       s = 0;
@@ -355,9 +448,9 @@ int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const in
     set_error("phikron_plan: half_step needs l_max >= 1");
     return PHIKRON_EINVAL;
   }
-  if (o.selector != PHIKRON_SELECT_PAPER) {
-    set_error("phikron_plan: selector MLP needs phikron_plan_select (not in this entry point)");
-    return PHIKRON_ENOTSUP;
+  if (o.selector != PHIKRON_SELECT_PAPER && o.selector != PHIKRON_SELECT_MLP) {
+    set_error("phikron_plan: bad selector");
+    return PHIKRON_EINVAL;
   }
   DeviceGuard dg(o.device);
   if (dg.rc != PHIKRON_OK) return dg.rc;
@@ -429,7 +522,7 @@ int phikron_plan_info(phikron_plan_t plan, phikron_info* info) {
   info->log10_bound = P.log10_bound;
   info->precision = P.opts.precision;
   info->quad = P.opts.quad;
-  info->selector_used = P.opts.selector;
+  info->selector_used = P.selector_used;
   info->unique_factors = P.nuniq;
   info->device_bytes = P.device_bytes;
   info->slices = P.mixed ? mixed_slices(P) : 0;
@@ -522,6 +615,17 @@ int phikron_setup_quadrature(double eps, int p, double alpha, double beta, int r
   clear_error();
   if (!s || !m || !cost) { set_error("phikron_setup_quadrature: NULL output"); return PHIKRON_EINVAL; }
   return planner::setup_quadrature(eps, p, alpha, beta, rule, s, m, cost);
+}
+
+int phikron_selector_features(int dims, const int* n, const double* tau_norm_inf, int l_max, double tol,
+                              float* out8) {
+  clear_error();
+  if ((dims != 2 && dims != 3) || !n || !tau_norm_inf || !out8 || l_max < 0 || !(tol > 0.0)) {
+    set_error("phikron_selector_features: bad arguments");
+    return PHIKRON_EINVAL;
+  }
+  selector_features(dims, n, tau_norm_inf, l_max, tol, out8);
+  return PHIKRON_OK;
 }
 
 int phikron_gauss_legendre(int m, double* x, double* w) {

@@ -50,6 +50,19 @@ int gauss_legendre(int m, double* x, double* w);
 int clenshaw_curtis(int n, double* x, double* w);
 }  // namespace planner
 
+// ----------------------------------------------------------------------------- selector
+namespace selector {
+double criterion(double zlo, double zhi, int p, int s, int m, int npts);
+int search(double zlo, double zhi, int p, double tol, int npts, int* s, int* m, int* cost);
+}  // namespace selector
+namespace mlp {
+int forward(const float* dparams, const float* dX, int count, float* dlogits, int* ds, int* dm, cudaStream_t st);
+bool model(std::vector<float>* out);
+}  // namespace mlp
+// 8 selector features: log10(tau ||A^d||_inf) (d = 1..3; -6 for a missing axis), log2(n_d)/8,
+// l_max/4, -log10(tol)/10
+void selector_features(int dims, const int* n, const double* tau_norm_inf, int p, double tol, float* out);
+
 // ----------------------------------------------------------------------------- fp64 GEMM
 // C[z](i, j) = alpha * sum_k A[z](i, k) * B[z](k, j) + beta * C[z](i, j), where the batch
 // index z = b * nb0 + i0 selects base offsets b*s?b + i0*s?i0 and the element (i, k) of A

@@ -17,6 +17,7 @@ struct Plan {
   double tol = 0.0;
   phikron_opts opts{};
   int s = 0, m = 0, cost = 0;
+  int selector_used = 0;   // 0 Algorithm 5, 1 network, 2 network with raised m, 3 network rejected -> Algorithm 5
   double alpha = 0.0, log10_bound = 0.0;
   std::vector<double> x, w, coef;   // nodes, weights on [0,1]; coef[(j-1)*m + k]
 

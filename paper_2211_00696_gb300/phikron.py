@@ -19,6 +19,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONVERGED, ENOTSUP = 0, -1, -2, -3, -4,
 QUAD_GAUSS, QUAD_CC = 0, 1
 PREC_FP64, PREC_OZAKI_BF16 = 0, 2
 SELECT_PAPER, SELECT_MLP = 0, 1
+SELECTOR_USED = {0: "algorithm5", 1: "network", 2: "network+m", 3: "fallback"}
 
 _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
              ENOTCONVERGED: "ENOTCONVERGED", ENOTSUP: "ENOTSUP"}
@@ -81,6 +82,19 @@ SIGNATURES = {
     "phikron_batch_get_info": (C.c_int, [C.c_void_p, C.POINTER(BatchInfo)]),
     "phikron_batch_check_status": (C.c_int, [C.c_void_p]),
     "phikron_batch_destroy": (None, [C.c_void_p]),
+    "phikron_selector_features": (C.c_int, [C.c_int, _IP, _DP, C.c_int, C.c_double, C.POINTER(C.c_float)]),
+    "phikron_selector_criterion": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _DP]),
+    "phikron_selector_search": (C.c_int, [C.c_int, _DP, _DP, _IP, _DP, C.c_int, C.c_int, _IP, _IP, _IP]),
+    "phikron_selector_param_count": (C.c_int, []),
+    "phikron_selector_set_model": (C.c_int, [C.POINTER(C.c_float), C.c_int]),
+    "phikron_selector_get_model": (C.c_int, [C.POINTER(C.c_float), C.c_int]),
+    "phikron_selector_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p]),
+    "phikron_selector_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]),
+    "phikron_selector_train": (C.c_int, [C.POINTER(C.c_float), _IP, _IP, C.c_int, C.c_int, C.c_int, C.c_float,
+                                         C.c_uint, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                         C.POINTER(C.c_float)]),
     "phikron_profile_begin": (C.c_int, [C.c_void_p, C.c_int]),
     "phikron_profile_end": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "phikron_log_quaderr": (C.c_int, [C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _DP]),
@@ -172,7 +186,7 @@ class Plan:
     def __init__(self, factors, tau: float, l_max: int, tol: float, *, precision: int = PREC_FP64,
                  quad: int = QUAD_GAUSS, force_s: int = -1, force_m: int = -1, alpha: float = 0.0,
                  beta: float = 0.0, device: int = -1, max_rhs: int = 1, slices: int = 0,
-                 half_step: bool = False):
+                 half_step: bool = False, selector: int = SELECT_PAPER):
         L = lib()
         self._h = C.c_void_p()
         facs = [np.ascontiguousarray(a, dtype=np.float64) for a in factors]
@@ -187,6 +201,7 @@ class Plan:
         o.quad, o.precision, o.force_s, o.force_m = quad, precision, force_s, force_m
         o.alpha, o.beta, o.device, o.max_rhs, o.slices = alpha, beta, device, max_rhs, slices
         o.half_step = 1 if half_step else 0
+        o.selector = selector
         _check(L.phikron_plan(C.byref(self._h), len(facs), ptrs, ns, tau, l_max, tol, C.byref(o)))
         self.shape = tuple(a.shape[0] for a in facs)
         self.N = int(np.prod(self.shape))

@@ -1,0 +1,156 @@
+"""GPU tests of the learned (s, m) selector: forward and gradient kernels against the oracle's
+float64 network, training on labels from the measured-criterion search, and what the trained
+network gains over Algorithm 5 on a 256^3 reaction-diffusion problem (both checked against the
+spectral oracle), plus the a-posteriori fallback.
+
+FP32 kernels vs float64 oracle: logits to 1e-4 relative; loss to 1e-5; gradient to 1e-3 in
+relative 2-norm (sums of 64 products in FP32 over a batch of 256)."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import phi as P
+from oracle import selector as OS
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _pk():
+    import paper_2211_00696_gb300 as pk
+    return pk
+
+
+def _lib():
+    from paper_2211_00696_gb300 import phikron as B
+    return B.lib(), B
+
+
+def _rand_params(seed):
+    rng = np.random.default_rng(seed)
+    p = rng.standard_normal(OS.n_params()) * 0.15
+    return p.astype(np.float32)
+
+
+def test_forward_kernel_matches_oracle():
+    L, B = _lib()
+    rng = np.random.default_rng(1)
+    params = _rand_params(2)
+    X = rng.standard_normal((300, 8)).astype(np.float32)
+    dp, dx = torch.from_numpy(params).cuda(), torch.from_numpy(X).cuda()
+    logits = torch.empty((300, 52), dtype=torch.float32, device="cuda")
+    s = torch.empty(300, dtype=torch.int32, device="cuda")
+    m = torch.empty(300, dtype=torch.int32, device="cuda")
+    assert L.phikron_selector_forward(dp.data_ptr(), dx.data_ptr(), 300, logits.data_ptr(), s.data_ptr(),
+                                      m.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    _, _, ref = OS.forward(params.astype(np.float64), X.astype(np.float64))
+    got = logits.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+    rs, rm = OS.predict(params.astype(np.float64), X.astype(np.float64))
+    srt = np.sort(ref[:, :21], axis=1)
+    clear = (srt[:, -1] - srt[:, -2]) > 1e-3
+    assert np.array_equal(s.cpu().numpy()[clear], rs[clear])
+    srt = np.sort(ref[:, 21:], axis=1)
+    clear = (srt[:, -1] - srt[:, -2]) > 1e-3
+    assert np.array_equal(m.cpu().numpy()[clear], rm[clear])
+
+
+def test_gradient_kernel_matches_oracle():
+    L, B = _lib()
+    rng = np.random.default_rng(3)
+    params = _rand_params(4)
+    X = rng.standard_normal((256, 8)).astype(np.float32)
+    ys = rng.integers(0, 21, 256).astype(np.int32)
+    ym = rng.integers(2, 33, 256).astype(np.int32)
+    t = lambda a: torch.from_numpy(a).cuda()
+    dp, dx, dys, dym = t(params), t(X), t(ys), t(ym)
+    grad = torch.empty(OS.n_params(), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    assert L.phikron_selector_grad(dp.data_ptr(), dx.data_ptr(), dys.data_ptr(), dym.data_ptr(), 256,
+                                   grad.data_ptr(), loss.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    p64, x64 = params.astype(np.float64), X.astype(np.float64)
+    ref_g = OS.grads(p64, x64, ys, ym)
+    ref_l = OS.loss(p64, x64, ys, ym)
+    assert abs(loss.item() / 256 - ref_l) <= 1e-5 * ref_l
+    g = grad.cpu().numpy()
+    assert np.linalg.norm(g - ref_g) <= 1e-3 * np.linalg.norm(ref_g)
+
+
+def _trained_model(pk, count=20000, epochs=60):
+    from paper_2211_00696_gb300 import selector as S
+    if S.load_default_model():
+        return "shipped"
+    X, s, m, _ = S.training_set(count, seed=21)
+    S.train(X, s, m, epochs=epochs, batch=256)
+    return "trained-in-test"
+
+
+def test_training_reduces_loss_and_predicts_labels():
+    from paper_2211_00696_gb300 import selector as S
+    X, s, m, _ = S.training_set(6000, seed=13)
+    params, loss = S.train(X[:5000], s[:5000], m[:5000], epochs=80, batch=256)
+    assert np.all(np.isfinite(params))
+    assert loss < 2.0, loss                      # from ln 21 + ln 31 = 6.5 at chance
+    ps, pm = OS.predict(params.astype(np.float64), X[5000:].astype(np.float64))
+    assert np.mean(np.abs(ps - s[5000:]) <= 1) >= 0.8
+    assert np.mean(np.abs(pm - m[5000:]) <= 1) >= 0.8
+
+
+@pytest.mark.parametrize("tol,slices", [(1e-6, 4), (1e-10, 5)])
+def test_selector_gain_on_256_cubed(tol, slices):
+    """The network's (s, m) costs no more than Algorithm 5's on a 256^3 reaction-diffusion
+    Laplacian and both meet the tolerance against the spectral oracle."""
+    pk = _pk()
+    src = _trained_model(pk)
+    shape, coeff, tau, p = (256, 256, 256), 0.05, 1e-3, 3
+    fac = [W.laplacian_factor(n, coeff) for n in shape]
+    v = W.uniform_vector(shape, 55)
+    exact = P.phi_spectral_dirichlet(shape, [coeff] * 3, tau, v, p)
+    res = {}
+    for sel in (pk.phikron.SELECT_PAPER, pk.phikron.SELECT_MLP):
+        plan = pk.Plan(fac, tau, p, tol, precision=pk.PREC_OZAKI_BF16, slices=slices, selector=sel)
+        info = plan.info()
+        V = torch.from_numpy(v).cuda()
+        out = plan.apply(V)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(3):
+            plan.apply(V, out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        errs = [P.rel_err_2(got[l], exact[l]) for l in range(p + 1)]
+        res[sel] = (info, e0.elapsed_time(e1) / 3, errs)
+        plan.close()
+    (ip, tp, ep), (im, tm, em) = res[pk.phikron.SELECT_PAPER], res[pk.phikron.SELECT_MLP]
+    print(f"model={src} tol={tol}: paper (s,m,C)=({ip['s']},{ip['m']},{ip['cost']}) {tp:.3f} ms err {max(ep):.2e}; "
+          f"mlp (s,m,C)=({im['s']},{im['m']},{im['cost']}) used={im['selector_used']} {tm:.3f} ms err {max(em):.2e}")
+    assert im["selector_used"] in (1, 2)
+    assert im["cost"] <= ip["cost"]
+    assert max(ep) <= 2 * tol + 1e-12 and max(em) <= 2 * tol + 1e-12
+
+
+def test_selector_fallbacks():
+    pk = _pk()
+    npar = OS.n_params()
+    from paper_2211_00696_gb300 import selector as S
+    S.set_model(np.zeros(npar, dtype=np.float32))     # predicts s = 0, m = 2 everywhere
+    shape = (64, 48, 32)
+    fac = [W.laplacian_factor(n, 0.5) for n in shape]
+    plan = pk.Plan(fac, 2e-3, 3, 1e-10, precision=pk.PREC_OZAKI_BF16, slices=5, selector=pk.phikron.SELECT_MLP)
+    assert plan.info()["selector_used"] == 3      # rejected by the a-posteriori check
+    v = W.uniform_vector(shape, 1)
+    out = plan.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+    exact = P.phi_spectral_dirichlet(shape, [0.5] * 3, 2e-3, v, 3)
+    assert max(P.rel_err_2(out[l], exact[l]) for l in range(4)) <= 1e-9
+    # nonsymmetric factors are outside the criterion: Algorithm 5 plans
+    cfac = [W.convdiff_factor(n) for n in (32, 32, 32)]
+    plan = pk.Plan(cfac, 1e-2, 3, 1e-8, precision=pk.PREC_OZAKI_BF16, selector=pk.phikron.SELECT_MLP)
+    assert plan.info()["selector_used"] == 3
+    _trained_model(pk)
