@@ -239,6 +239,35 @@ def run_batched(args):
                       "batch": info}), flush=True)
 
 
+def fp64_gpu_compare(prob, V, out_shape, flush, golden, dev, local, steps=3):
+    """The same workload on the float64 GPU path (float64 DFMA mode products), timed the same
+    way: the comparison the metric names (mixed vs FP64 GPU at the stated accuracy)."""
+    import torch
+
+    import paper_2211_00696_gb300 as pk
+    plan = pk.Plan(prob.factors, prob.tau, prob.l_max, PRECISIONS["fp64"][1], precision=pk.PREC_FP64,
+                   device=local)
+    Out = torch.empty(out_shape, dtype=torch.float64, device=dev)
+    plan.apply(V, Out)
+    torch.cuda.synchronize()
+    errs = sampled_rel_err(Out.cpu().numpy(), golden) if golden is not None else None
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        plan.apply(V, Out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    info = plan.info()
+    plan.close()
+    ms = tot / steps
+    return {"value": prob.N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "s": info["s"], "m": info["m"], "actions": info["actions"], "rel_err_sampled": errs}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -358,6 +387,8 @@ def run_ours(args):
             "e2e": {"value": world * prob.N / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": prob.N * 8, "d2h_bytes_per_step": (prob.l_max + 1) * prob.N * 8},
         }
+        if args.fp64_compare and args.precision != "fp64":
+            line["fp64_gpu"] = fp64_gpu_compare(prob, V, Out.shape, flush, golden, dev, local)
         if args.cpu_baseline and world == 1:
             from oracle import planner as PL
             s, m, _ = PL.setup_quadrature(prob.tol, prob.l_max, PL.alpha_inf(prob.factors, prob.tau))
@@ -380,7 +411,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
+    ap.add_argument("--precision", default="mixed", choices=list(PRECISIONS))
+    ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", default="convdiff3d", choices=["convdiff3d", "batched"])
     args = ap.parse_args()

@@ -195,6 +195,7 @@ typedef struct phikron_batch_info {
   int       tuned;        /* 1 once the autotuner has run (or was not requested)             */
   double    best_ms;      /* time of the chosen shape during tuning (0 if not tuned)          */
   size_t    device_bytes; /* device memory held by the batch                                 */
+  int       ws_kernel;    /* 1 if the chosen mode kernel is the warp-specialised variant     */
 } phikron_batch_info;
 
 int  phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* plans, int nrhs,

@@ -148,18 +148,23 @@ int phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // candidate launch shapes
     std::vector<SeqConfig> cfgs;
-    for (int sub : {1, 2}) {
-      if (sub == 2 && slices != 3) continue;
-      for (bool bf : {false, true}) {
-        for (int g : {nsm, (3 * nsm) / 4}) {
-          SeqConfig c;
-          c.half = B->half;
-          c.slices = slices;
-          c.sub = sub;
-          c.grid = g;
-          c.big_first = bf;
-          c.graph = true;
-          cfgs.push_back(c);
+    const bool ws0 = mode_kernel_ws_default();
+    for (bool ws : {ws0, !ws0}) {
+      for (int sub : {1, 2}) {
+        if (sub == 2 && (slices != 3 || ws)) continue;  // 64-wide chunks: single-role kernel only
+        for (bool bf : {false, true}) {
+          for (int g : {nsm, (3 * nsm) / 4}) {
+            SeqConfig c;
+            c.half = B->half;
+            c.slices = slices;
+            c.sub = sub;
+            c.grid = g;
+            c.big_first = bf;
+            c.graph = true;
+            c.ws = ws;
+            cfgs.push_back(c);
+            if (!autotune) break;
+          }
           if (!autotune) break;
         }
         if (!autotune) break;
@@ -254,6 +259,7 @@ int phikron_batch_get_info(phikron_batch_t b, phikron_batch_info* info) {
   size_t bytes = b->work_bytes;
   for (const auto& s : b->cand) bytes += s->device_bytes;
   info->device_bytes = bytes;
+  info->ws_kernel = c.ws ? 1 : 0;
   return PHIKRON_OK;
 }
 

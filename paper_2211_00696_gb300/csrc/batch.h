@@ -53,6 +53,7 @@ struct SeqConfig {
   int grid = 148;         // CTAs per mode pass
   bool big_first = false; // order the jobs of a pass by decreasing tile count
   bool graph = true;      // capture the sequence as a CUDA graph
+  bool ws = true;         // warp-specialised mode kernel
 };
 
 struct MixedView {
@@ -63,6 +64,10 @@ struct MixedView {
   const float2* coef;
   int slices, nsm;
 };
+
+// Mode-kernel variant when nothing is tuned: the warp-specialised one, unless the environment
+// variable PHIKRON_MODE_KERNEL is "classic" (the single-role kernel).
+bool mode_kernel_ws_default();
 
 const MixedView mixed_view(const Plan& P, int d);
 int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& cfg);

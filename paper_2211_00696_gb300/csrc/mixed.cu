@@ -10,8 +10,9 @@
 // Each kernel that writes a state vector also records an exponent e with |v| < 2^e
 // (atomicMax over the vector), which the next mode product uses to cut its digits.
 #include <algorithm>
-#include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <cmath>
 #include <vector>
 
 #include "mixed.h"
@@ -431,6 +432,7 @@ int precision_setup(Plan& P) {
   cfg.grid = M->nsm;
   cfg.big_first = false;
   cfg.graph = true;
+  cfg.ws = mode_kernel_ws_default();
   PK_RET(seq_build(M->seq, units, 1, cfg));
   return PHIKRON_OK;
 }
@@ -534,6 +536,11 @@ struct Builder {
 // outputs) over `units` (one unit = one vector of one plan).  Unit u reads V from pointer
 // table entry 2*inst at byte offset rhs*N*8 and writes Out to entry 2*inst+1 at offset
 // rhs*(p+1)*(1+half)*N*8.
+bool mode_kernel_ws_default() {
+  const char* v = std::getenv("PHIKRON_MODE_KERNEL");
+  return !(v && std::strcmp(v, "classic") == 0);
+}
+
 int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& cfg) {
   Builder B;
   B.big_first = cfg.big_first;
@@ -676,6 +683,7 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       sh.grid = cfg.grid;
       sh.in_f64 = (d == 0) && first_f64;
       sh.trans = trans;
+      sh.ws = cfg.ws;
       if (dims == 1) sh.trans = false;
       // all jobs of one pass share the formulation (same axis d)
       B.mode_step(jobs, sh);

@@ -37,6 +37,7 @@ struct PassShape {
   int sub;                 // K chunk = 32 * sub (1, or 2 with 3 slices)
   int grid;                // CTAs (persistent, 1 per SM at most)
   bool in_f64, trans;
+  bool ws;                 // warp-specialised kernel (producer / MMA / epilogue warps)
 };
 
 constexpr int MAX_PTRS = 128;

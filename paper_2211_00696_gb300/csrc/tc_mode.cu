@@ -3,8 +3,10 @@
 //
 // A mode product out[b][i0][i][r] = sum_k E[i][k] in[b][i0][k][r] is computed with both
 // operands cut into KS "digit" slices:
-//   in  ~ 2^{eX}   * sum_t x_t,  x_t = +-d_t 2^{-8t}, d_t in [0, 255]   (per-vector exponent eX;
-//        the digits are those of |in| * 2^{-eX} rounded to nearest at digit KS)
+//   in  ~ 2^{eX}   * sum_t x_t,  x_t = integer * 2^{-8t}, |integer| <= 256   (per-vector
+//        exponent eX; float64 input: the sign-magnitude digits of |in| 2^{-eX} rounded to
+//        nearest at digit KS, cut with integer ops; float-float input: signed digits from
+//        FP32 round-to-nearest remainders)
 //   E   ~ 2^{f_i}  * sum_s e_s,  e_s likewise                           (per-row exponent f_i)
 // Every slice value is exactly representable in BF16.  The slice pairs (s, t) with
 // s + t <= KS + 1 are multiplied on the tensor cores (kind::f16, BF16 inputs, FP32
@@ -17,9 +19,9 @@
 // FP32) arithmetic and scales by 2^{eX + f_i}.  Result accuracy per product is
 // about 2^{1-8 KS} relative to ||E||_inf max|in|: KS = 3 ~ FP32, KS = 5 ~ 1e-12.
 //
-// No float64 arithmetic runs per element (GB300 executes float64 at ~1/64 of FP32): the
-// digits are cut from the float64 or float-float bit patterns with integer shifts, and the
-// state between passes is float-float (hi, lo) FP32 pairs.
+// No float64 arithmetic runs per element (GB300 executes float64 at ~1/64 of FP32): float64
+// digits are cut from the bit patterns with integer shifts, float-float digits with FP32
+// adds, and the state between passes is float-float (hi, lo) FP32 pairs.
 //
 // Two formulations share one kernel:
 //   TRANS (R > 1, contraction over a non-fastest axis):  D[r][i] = sum_k X^T[r][k] E[i][k]
@@ -131,11 +133,6 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // F = |x| * 2^{64 - eX} as a 64-bit fixed-point integer (|x| < 2^eX); the digits d_t are the
 // bytes of F, most significant first.
 
-// m * 2^sh for a 24-bit m and sh <= 40 (bits below 2^0 are dropped)
-__device__ __forceinline__ uint64_t place24(uint32_t m, int sh) {
-  return sh >= 0 ? ((uint64_t)m << sh) : (uint64_t)(m >> min(-sh, 31));
-}
-
 // float64 input; eb = 1011 + eX
 __device__ __forceinline__ uint64_t fixed_f64(double x, int eb, uint32_t& sgn) {
   const uint64_t b = (uint64_t)__double_as_longlong(x);
@@ -144,18 +141,6 @@ __device__ __forceinline__ uint64_t fixed_f64(double x, int eb, uint32_t& sgn) {
   const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull);
   const int sh = ex - eb;  // <= 11
   return sh >= 0 ? (m << sh) : (m >> min(-sh, 63));
-}
-
-// float-float input (hi, lo) with |lo| <= ulp(hi)/2; eb = 86 + eX
-__device__ __forceinline__ uint64_t fixed_ff(float hi, float lo, int eb, uint32_t& sgn) {
-  const uint32_t bh = __float_as_uint(hi), bl = __float_as_uint(lo);
-  sgn = bh & 0x80000000u;
-  const uint32_t eh = (bh >> 23) & 0xFFu, el = (bl >> 23) & 0xFFu;
-  const uint32_t mh = (bh & 0x7FFFFFu) | (eh ? 0x800000u : 0u);
-  const uint32_t ml = (bl & 0x7FFFFFu) | (el ? 0x800000u : 0u);
-  const uint64_t Fh = place24(mh, (int)eh - eb);
-  const uint64_t Fl = place24(ml, (int)el - eb);
-  return ((bh ^ bl) & 0x80000000u) ? Fh - Fl : Fh + Fl;
 }
 
 // round to nearest at digit KS, saturating on carry-out
@@ -184,6 +169,39 @@ __device__ __forceinline__ void cut_pair(uint64_t F0, uint32_t s0, uint64_t F1, 
     out[T - 1] = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632u);  // (bf16(b) << 16) | bf16(a)
     cut_pair<KS, T + 1>(F0, s0, F1, s1, out);
   }
+}
+
+// Float-float input: the slices come from FP32 arithmetic alone.  With X = (hi + lo) 2^{-eX}
+// (|X| < 1), slice t is X's running remainder rounded to a multiple of 2^{-8t} by adding and
+// subtracting 1.5 * 2^{23-8t} (round to nearest in FP32); the remainder update is exact.  lo
+// joins the remainder before slice min(4, KS), where the FP32 add rounds at <= 2^-49.  Every
+// slice is an integer of at most 256 times 2^{-8t}, exact in BF16, like the integer digits.
+template <int KS>
+__device__ __forceinline__ void cut_ff_float(float hi, float lo, float sc, float* v) {
+  float r = __fmul_rn(hi, sc);
+  const float l = __fmul_rn(lo, sc);
+  constexpr int FOLD = KS < 4 ? KS : 4;
+#pragma unroll
+  for (int t = 1; t <= KS; ++t) {
+    if (t == FOLD) r = __fadd_rn(r, l);
+    const float M = __uint_as_float((uint32_t)(127 + 23 - 8 * t) << 23) * 1.5f;
+    const float q = __fsub_rn(__fadd_rn(r, M), M);
+    v[t - 1] = q;
+    r = __fsub_rn(r, q);
+  }
+}
+
+// two FP32 values exactly representable in BF16 -> (bf16(b) << 16) | bf16(a)
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+  return d;
+}
+
+// 2^e for e in [-149, 127] (subnormal scales included)
+__device__ __forceinline__ float pow2f_full(int e) {
+  e = e < -149 ? -149 : (e > 127 ? 127 : e);
+  return e >= -126 ? __uint_as_float((uint32_t)(e + 127) << 23) : __uint_as_float(1u << (e + 149));
 }
 
 // ---------------------------------------------------------------- float-float helpers
@@ -372,7 +390,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
       scale_s[tid] = pow2f(E);
     }
     const uint32_t idesc = TRANS ? make_idesc(128, nrows_e) : make_idesc(128, 128);
-    const int eb = IN_F64 ? 1011 + T.eX : 86 + T.eX;
+    const int eb = 1011 + T.eX;           // float64 input: integer digit cutting
+    const float xsc = pow2f_full(-T.eX);  // float-float input: FP32 slicing of X 2^{-eX}
     bool init[4] = {false, false, false, false};
     TileCtx Tn = T;
     const long long next_tile = tile + gridDim.x;
@@ -410,21 +429,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
         uint32_t pk[KS][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-          uint32_t s0, s1;
-          uint64_t F0, F1;
           if (IN_F64) {
-            F0 = fixed_f64(raw[q].d[e], eb, s0);
-            F1 = fixed_f64(raw[q].d[e + 1], eb, s1);
-          } else {
-            F0 = fixed_ff(raw[q].f[e].x, raw[q].f[e].y, eb, s0);
-            F1 = fixed_ff(raw[q].f[e + 1].x, raw[q].f[e + 1].y, eb, s1);
-          }
-          F0 = round_digits<KS>(F0);
-          F1 = round_digits<KS>(F1);
-          uint32_t w[KS];
-          cut_pair<KS>(F0, s0, F1, s1, w);
+            uint32_t s0, s1;
+            const uint64_t F0 = round_digits<KS>(fixed_f64(raw[q].d[e], eb, s0));
+            const uint64_t F1 = round_digits<KS>(fixed_f64(raw[q].d[e + 1], eb, s1));
+            uint32_t w[KS];
+            cut_pair<KS>(F0, s0, F1, s1, w);
 #pragma unroll
-          for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
+            for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
+          } else {
+            float v0[KS], v1[KS];
+            cut_ff_float<KS>(raw[q].f[e].x, raw[q].f[e].y, xsc, v0);
+            cut_ff_float<KS>(raw[q].f[e + 1].x, raw[q].f[e + 1].y, xsc, v1);
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v0[sl], v1[sl]);
+          }
         }
         const uint32_t off = (uint32_t)(orow >> 3) * 512u + (uint32_t)kq * 128u + (uint32_t)(orow & 7) * 16u;
 #pragma unroll
@@ -499,7 +518,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
         tmem_ld16(lane_base + (uint32_t)cc, d2);
         tmem_ld16(lane_base + 128u + (uint32_t)cc, d3);
         tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
-        tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
+        if (KS >= 4) {
+          tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
+        } else {  // KS = 3 has no pair at level >= 5: the fourth accumulator is never written
+#pragma unroll
+          for (int j = 0; j < 16; ++j) d5[j] = 0.0f;
+        }
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -563,6 +587,424 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ---------------------------------------------------------------- warp-specialised variant
+// Roles (14 warps = 448 threads, 128 registers a thread; 32-wide K chunks):
+//   warps 0-7   producers: cut the operand digits of each chunk into the 2-stage ring;
+//               producer thread 0 also starts the chunk's E bulk copy
+//   warps 8-11  epilogue: drain the four TMEM accumulators (warp 8+q owns TMEM lanes 32q..32q+31,
+//               all columns), float-float, scale, store, exponent of the output
+//   warp 12     lane 0 issues the tcgen05 MMAs
+//   warp 13     lane 0 resolves each tile's context (job lookup, input exponent, pointers) into a
+//               4-slot shared-memory ring ahead of the other roles, so that no role waits on a
+//               chain of dependent global loads at a tile boundary
+// mbarriers: full_x[2] (256 producer arrivals), full_e[2] (bulk-copy bytes), empty[2] (MMA
+// commit), tmem_full (MMA commit after a tile), tmem_empty (128 epilogue arrivals), done (final
+// MMA commit), slot_full[4] (scheduler), slot_empty[4] (every reader: 256 + 1 + 128).  The
+// producers fill the ring for the next tile while the epilogue drains the current one.  Every
+// wait is bounded; an expired wait sets a shared abort flag and the status word, every role
+// stops at its next check, the epilogue decides by a vote so that its named barrier stays
+// matched, and TMEM is freed only after the MMA thread saw its own MMAs complete.
+constexpr int WS_EPI0 = 8, WS_MMA = 12, WS_SCHED = 13, WS_THREADS = 448;
+constexpr int WS_PROD = 256, WS_EPI = 128, WS_SLOTS = 4;
+constexpr int WS_SLOT_READERS = WS_PROD + 1 + WS_EPI;
+
+struct WsSlot {
+  const void* in;
+  void* out;
+  const uint8_t* ebase;  // E slices of the tile's 128-row half
+  const int* rexp;       // row exponents of that half
+  int* out_exp;
+  long long R, B0;
+  long long base;        // TRANS: b0 * n * R (first element of the tile's slab); NORMAL: 0
+  long long g0;          // first fiber of the tile: r0 (TRANS) or row0 (NORMAL)
+  int n, nsub, half, eX, nrows_e, out_f64;
+};
+
+// shared-memory layout after the two stages
+constexpr int WS_BAR_BYTES = 256, WS_SCALE_BYTES = 512, WS_SLOT_BYTES = 512;
+static_assert(sizeof(WsSlot) * WS_SLOTS <= WS_SLOT_BYTES, "slot ring");
+
+size_t ws_smem_bytes(int ks) {
+  return (size_t)2 * 2 * ks * SLICE_BYTES + WS_BAR_BYTES + WS_SCALE_BYTES + WS_SLOT_BYTES + 32;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// all 128 epilogue threads (named barrier 1): true if any of them passes true
+__device__ __forceinline__ bool epi_vote_any(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, 1, 128, q;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void ws_fail(volatile int* abort_s, int* status) {
+  *abort_s = 1;
+  atomicExch(status, PHIKRON_ETIMEOUT);
+}
+
+// read slot tc % WS_SLOTS once it is filled, then release it
+__device__ __forceinline__ bool ws_get(const WsSlot* slots, uint64_t* slot_full, uint64_t* slot_empty, uint32_t tc,
+                                       WsSlot& out) {
+  const uint32_t q = tc % WS_SLOTS;
+  const bool ok = mbar_wait(smem_u32(&slot_full[q]), (tc / WS_SLOTS) & 1u);
+  if (ok) out = slots[q];
+  mbar_arrive(smem_u32(&slot_empty[q]));
+  return ok;
+}
+
+// raw operand values of one thread: 8 consecutive k (from kc) of its operand row
+template <bool IN_F64, bool TRANS>
+__device__ __forceinline__ void ws_load(const WsSlot& S, int orow, int kc, Raw<IN_F64>& raw) {
+  const long long gr = S.g0 + orow;
+  const bool vr = TRANS ? (gr < S.R) : (gr < S.B0);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int k = kc + e;
+    const bool ok = vr && k < S.n;
+    const long long idx = TRANS ? S.base + (long long)k * S.R + gr : gr * (long long)S.n + k;
+    if (IN_F64)
+      raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(S.in) + idx) : 0.0;
+    else
+      raw.f[e] = ok ? __ldg(reinterpret_cast<const float2*>(S.in) + idx) : make_float2(0.f, 0.f);
+  }
+}
+
+// hi + lo ~ d2 + d3 + d4 + d5 (the level accumulators, largest first)
+template <int KS>
+__device__ __forceinline__ void ff_combine(float d2, float d3, float d4, float d5, float& hi, float& lo) {
+  float t45 = d4, e45 = 0.0f, u, eu, eh;
+  if (KS >= 4) two_sum(d4, d5, t45, e45);
+  two_sum(d3, t45, u, eu);
+  two_sum(d2, u, hi, eh);
+  lo = eh + (eu + e45);
+  fast_two_sum(hi, lo, hi, lo);
+}
+
+template <int KS, bool IN_F64, bool TRANS>
+__global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int HALF_BYTES = KS * SLICE_BYTES;
+  constexpr int STAGE_BYTES = 2 * HALF_BYTES;
+  uint8_t* tail = smem + 2 * STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
+  uint64_t* full_x = bars;        // [2]
+  uint64_t* full_e = bars + 2;    // [2]
+  uint64_t* empty = bars + 4;     // [2]
+  uint64_t* tmem_full = bars + 6;
+  uint64_t* tmem_empty = bars + 7;
+  uint64_t* done = bars + 8;
+  uint64_t* slot_full = bars + 9;    // [WS_SLOTS]
+  uint64_t* slot_empty = bars + 13;  // [WS_SLOTS]
+  float* scale_s = reinterpret_cast<float*>(tail + WS_BAR_BYTES);  // 128 floats
+  WsSlot* slots = reinterpret_cast<WsSlot*>(tail + WS_BAR_BYTES + WS_SCALE_BYTES);
+  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(tail + WS_BAR_BYTES + WS_SCALE_BYTES + WS_SLOT_BYTES);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(tail + WS_BAR_BYTES + WS_SCALE_BYTES + WS_SLOT_BYTES + 16);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long total_tiles = P.total_tiles;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_x[q])), "r"(WS_PROD));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_e[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(tmem_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tmem_empty)), "r"(WS_EPI));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
+    for (int q = 0; q < WS_SLOTS; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&slot_empty[q])), "r"(WS_SLOT_READERS));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *abort_s = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_s)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_s;
+
+  if (warp < WS_EPI0) {
+    // ------------------------------------------------------------ producers
+    const int orow = tid & 127;
+    const int kh = tid >> 7;  // k-groups 2*kh, 2*kh + 1 of every 32-wide chunk
+    uint32_t it = 0, tc = 0;
+    int e_last = -1;          // thread 0: chunk of the latest E bulk copy
+    long long tile = blockIdx.x;
+    WsSlot S, Sn;
+    Raw<IN_F64> raw[2];
+    bool have = false;
+    if (tile < total_tiles) {
+      have = ws_get(slots, slot_full, slot_empty, 0, S);
+      if (!have) {
+        ws_fail(abort_s, status);
+      } else {
+        ws_load<IN_F64, TRANS>(S, orow, 16 * kh, raw[0]);
+        ws_load<IN_F64, TRANS>(S, orow, 16 * kh + 8, raw[1]);
+      }
+    }
+    for (; have && tile < total_tiles; tile += gridDim.x, ++tc) {
+      const int nchunks = S.nsub;
+      const int eb = 1011 + S.eX;
+      const float xsc = pow2f_full(-S.eX);
+      const bool has_next = tile + gridDim.x < total_tiles;
+      bool stop = false;
+      for (int c = 0; c < nchunks; ++c, ++it) {
+        const uint32_t st = it & 1u, use = it >> 1;
+        uint8_t* sX = smem + st * STAGE_BYTES;
+        uint8_t* sE = sX + HALF_BYTES;
+        if (use >= 1 && !mbar_wait(smem_u32(&empty[st]), (use - 1) & 1u)) ws_fail(abort_s, status);
+        if (*abort_s) { stop = true; break; }
+        if (tid == 0) {
+          e_last = (int)it;
+          mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)HALF_BYTES);
+          bulk_copy_g2s(smem_u32(sE), S.ebase + (size_t)c * HALF_BYTES, (uint32_t)HALF_BYTES, smem_u32(&full_e[st]));
+        }
+        Raw<IN_F64> rawn[2];
+        if (c + 1 < nchunks) {
+          ws_load<IN_F64, TRANS>(S, orow, 32 * (c + 1) + 16 * kh, rawn[0]);
+          ws_load<IN_F64, TRANS>(S, orow, 32 * (c + 1) + 16 * kh + 8, rawn[1]);
+        } else if (has_next) {
+          if (ws_get(slots, slot_full, slot_empty, tc + 1, Sn)) {
+            ws_load<IN_F64, TRANS>(Sn, orow, 16 * kh, rawn[0]);
+            ws_load<IN_F64, TRANS>(Sn, orow, 16 * kh + 8, rawn[1]);
+          } else {
+            ws_fail(abort_s, status);
+          }
+        }
+#pragma unroll
+        for (int g2 = 0; g2 < 2; ++g2) {
+          uint32_t pk[KS][4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            if (IN_F64) {
+              uint32_t s0, s1;
+              const uint64_t F0 = round_digits<KS>(fixed_f64(raw[g2].d[e], eb, s0));
+              const uint64_t F1 = round_digits<KS>(fixed_f64(raw[g2].d[e + 1], eb, s1));
+              uint32_t w[KS];
+              cut_pair<KS>(F0, s0, F1, s1, w);
+#pragma unroll
+              for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
+            } else {
+              float v0[KS], v1[KS];
+              cut_ff_float<KS>(raw[g2].f[e].x, raw[g2].f[e].y, xsc, v0);
+              cut_ff_float<KS>(raw[g2].f[e + 1].x, raw[g2].f[e + 1].y, xsc, v1);
+#pragma unroll
+              for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v0[sl], v1[sl]);
+            }
+          }
+          const int g = 2 * kh + g2;
+          const uint32_t off = (uint32_t)(orow >> 3) * 512u + (uint32_t)g * 128u + (uint32_t)(orow & 7) * 16u;
+#pragma unroll
+          for (int sl = 0; sl < KS; ++sl)
+            *reinterpret_cast<uint4*>(sX + sl * SLICE_BYTES + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&full_x[st]));
+        raw[0] = rawn[0];
+        raw[1] = rawn[1];
+      }
+      if (stop) break;
+      S = Sn;
+    }
+    if (tid == 0 && *abort_s) {
+      // bulk copies still in flight must land before the CTA's shared memory is released
+      for (int k = e_last; k >= 0 && k >= e_last - 1; --k)
+        mbar_wait(smem_u32(&full_e[k & 1]), ((uint32_t)k >> 1) & 1u);
+    }
+  } else if (warp < WS_MMA) {
+    // ------------------------------------------------------------ epilogue
+    const int et = tid - WS_EPI0 * 32;   // 0..127 = TMEM lane
+    const uint32_t lane_base = tmem + ((uint32_t)((et >> 5) * 32) << 16);
+    uint32_t tc = 0;
+    for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++tc) {
+      WsSlot S;
+      bool ok = ws_get(slots, slot_full, slot_empty, tc, S);
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // the previous tile's scale table is no longer read
+      if (ok) scale_s[et] = pow2f(S.eX + ((et < S.nrows_e) ? S.rexp[et] : 0));
+      ok = ok && mbar_wait(smem_u32(tmem_full), tc & 1u);
+      if (!ok) ws_fail(abort_s, status);
+      // the vote is also the barrier after the scale writes; every epilogue thread decides alike
+      if (epi_vote_any(!ok || *abort_s)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t mx = 0;   // largest |hi| bit pattern stored
+      if (TRANS) {
+        // TMEM lane = fiber r, column = output row i of this half; stores coalesce over lanes
+        const long long g = S.g0 + et;
+        const bool vg = g < S.R;
+        const long long o0 = S.base + (long long)(128 * S.half) * S.R + g;
+        for (int cc = 0; cc < S.nrows_e; cc += 16) {
+          float d2[16], d3[16], d4[16], d5[16];
+          tmem_ld16(lane_base + (uint32_t)cc, d2);
+          tmem_ld16(lane_base + 128u + (uint32_t)cc, d3);
+          tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
+          if (KS >= 4) tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
+          tmem_wait_ld();
+          if (vg) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float hi, lo;
+              ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
+              const float sc = scale_s[cc + j];
+              hi *= sc;
+              lo *= sc;
+              const long long oidx = o0 + (long long)(cc + j) * S.R;
+              if (S.out_f64)
+                reinterpret_cast<double*>(S.out)[oidx] = ff_to_f64(hi, lo);
+              else
+                reinterpret_cast<float2*>(S.out)[oidx] = make_float2(hi, lo);
+              mx = max(mx, __float_as_uint(hi) & 0x7FFFFFFFu);
+            }
+          }
+        }
+      } else {
+        // TMEM lane = output row i of this half, column = fiber; stores coalesce over lanes
+        const bool vi = et < S.nrows_e;
+        const int ncols = (int)min(128LL, S.B0 - S.g0);
+        const float sc = scale_s[et];
+        const long long o0 = S.g0 * (long long)S.n + 128 * S.half + et;
+        for (int cc = 0; cc < ncols; cc += 16) {
+          float d2[16], d3[16], d4[16], d5[16];
+          tmem_ld16(lane_base + (uint32_t)cc, d2);
+          tmem_ld16(lane_base + 128u + (uint32_t)cc, d3);
+          tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
+          if (KS >= 4) tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
+          tmem_wait_ld();
+          if (vi) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (cc + j >= ncols) break;
+              float hi, lo;
+              ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
+              hi *= sc;
+              lo *= sc;
+              const long long oidx = o0 + (long long)(cc + j) * S.n;
+              if (S.out_f64)
+                reinterpret_cast<double*>(S.out)[oidx] = ff_to_f64(hi, lo);
+              else
+                reinterpret_cast<float2*>(S.out)[oidx] = make_float2(hi, lo);
+              mx = max(mx, __float_as_uint(hi) & 0x7FFFFFFFu);
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(tmem_empty));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      // |v| < 2^{biased - 126}; a zero vector keeps the slot's initial (very negative) value
+      const int emax = (int)(mx >> 23);
+      if (lane == 0 && S.out_exp && emax > 0) atomicMax(S.out_exp, emax - 126);
+    }
+  } else if (warp == WS_MMA) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- MMA issuer
+      uint32_t it = 0, tc = 0;
+      bool issued = false;
+      for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++tc) {
+        WsSlot S;
+        if (!ws_get(slots, slot_full, slot_empty, tc, S)) ws_fail(abort_s, status);
+        if (tc >= 1 && !mbar_wait(smem_u32(tmem_empty), (tc - 1) & 1u)) ws_fail(abort_s, status);
+        if (*abort_s) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idesc = TRANS ? make_idesc(128, S.nrows_e) : make_idesc(128, 128);
+        bool init[4] = {false, false, false, false};
+        bool stop = false;
+        for (int c = 0; c < S.nsub; ++c, ++it) {
+          const uint32_t st = it & 1u, use = it >> 1;
+          if (!mbar_wait(smem_u32(&full_x[st]), use & 1u) || !mbar_wait(smem_u32(&full_e[st]), use & 1u))
+            ws_fail(abort_s, status);
+          if (*abort_s) { stop = true; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t xa = smem_u32(smem + st * STAGE_BYTES), ea = xa + HALF_BYTES;
+#pragma unroll
+          for (int s = 1; s <= KS; ++s) {
+#pragma unroll
+            for (int t = 1; t <= KS; ++t) {
+              if (s + t > KS + 1) continue;
+              const int L = s + t - 2;
+              const int a = L < 3 ? L : 3;
+              const uint32_t dacc = tmem + (uint32_t)(a * 128);
+#pragma unroll
+              for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t xd = make_desc(xa + (uint32_t)((t - 1) * SLICE_BYTES + ks * 256));
+                const uint64_t ed = make_desc(ea + (uint32_t)((s - 1) * SLICE_BYTES + ks * 256));
+                if (TRANS)
+                  mma_bf16(dacc, xd, ed, idesc, init[a] ? 1u : 0u);
+                else
+                  mma_bf16(dacc, ed, xd, idesc, init[a] ? 1u : 0u);
+                init[a] = true;
+                issued = true;
+              }
+            }
+          }
+          mma_commit(smem_u32(&empty[st]));
+        }
+        if (stop) break;
+        mma_commit(smem_u32(tmem_full));
+      }
+      // every MMA this thread issued is complete before TMEM is released
+      mma_commit(smem_u32(done));
+      if (issued) mbar_wait(smem_u32(done), 0u);
+    }
+  } else if (warp == WS_SCHED && lane == 0) {
+    // ------------------------------------------------------------ scheduler (warp 13, lane 0)
+    int job = 0;
+    uint32_t tc = 0;
+    for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++tc) {
+      const uint32_t q = tc % WS_SLOTS;
+      if (tc >= WS_SLOTS && !mbar_wait(smem_u32(&slot_empty[q]), ((tc / WS_SLOTS) - 1) & 1u))
+        ws_fail(abort_s, status);
+      if (*abort_s) break;
+      // tiles of this CTA increase, so the job index only moves forward
+      int lo = job, hi = P.njobs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.jobs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+      }
+      job = lo;
+      const GJob& J = P.jobs[job];
+      const long long tj = tile - J.tile_begin;
+      const long long rtiles = TRANS ? (J.R + 127) / 128 : 1;
+      const long long per_half = TRANS ? J.B0 * rtiles : (J.B0 + 127) / 128;
+      const int half = (int)(tj / per_half);
+      const long long th = tj % per_half;
+      WsSlot& S = slots[q];
+      S.in = (J.in_tab >= 0) ? (const void*)((const char*)P.ptrtab[J.in_tab] + J.tab_off_in) : J.in;
+      S.out = (J.out_tab >= 0) ? (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out) : J.out;
+      const int nsub = (J.n + 31) / 32;
+      S.ebase = J.eslices + (size_t)half * (size_t)nsub * KS * SLICE_BYTES;
+      S.rexp = J.rexp + 128 * half;
+      S.out_exp = J.out_exp;
+      S.R = J.R;
+      S.B0 = J.B0;
+      S.base = TRANS ? (th / rtiles) * (long long)J.n * J.R : 0;
+      S.g0 = TRANS ? (th % rtiles) * 128 : th * 128;
+      S.n = J.n;
+      S.nsub = nsub;
+      S.half = half;
+      const int eX = *J.in_exp;
+      S.eX = eX < -600 ? 0 : eX;  // all-zero input
+      S.nrows_e = min(128, J.n - 128 * half);
+      S.out_f64 = J.out_f64;
+      mbar_arrive(smem_u32(&slot_full[q]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 __global__ void ptrtab_set_kernel(void** tab, PtrArgs args) {
   const int i = threadIdx.x;
   if (i < args.n) tab[i] = args.p[i];
@@ -571,34 +1013,36 @@ __global__ void ptrtab_set_kernel(void** tab, PtrArgs args) {
 }  // namespace
 
 size_t smem_bytes(int ks, int sub) {
-  return (size_t)2 * 2 * sub * ks * SLICE_BYTES + 64 + 512 + 16 + 16;
+  return (size_t)2 * 2 * sub * ks * SLICE_BYTES + 128 + 512 + 16 + 16 + 16;
 }
 
 template <int KS, int SUB, bool IN_F64, bool TRANS>
-int launch_one(const GPass& P, int grid, int* status, cudaStream_t st) {
-  const size_t sm = smem_bytes(KS, SUB);
-  auto kern = mode_kernel<KS, SUB, IN_F64, TRANS>;
-  static bool attr = false;  // per instantiation
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) {
-      set_error(std::string("tc mode kernel smem attribute: ") + cudaGetErrorString(e));
-      return PHIKRON_ECUDA;
-    }
-    attr = true;
+int launch_one(const GPass& P, int grid, bool ws, int* status, cudaStream_t st) {
+  // the warp-specialised kernel is built for 32-wide K chunks only (its 14 warps leave 128
+  // registers a thread, too few for the doubled raw-value buffers of 64-wide chunks)
+  const bool use_ws = ws && SUB == 1;
+  const size_t sm = use_ws ? ws_smem_bytes(KS) : smem_bytes(KS, SUB);
+  auto kern = use_ws ? mode_kernel_ws<KS, IN_F64, TRANS> : mode_kernel<KS, SUB, IN_F64, TRANS>;
+  const int threads = use_ws ? WS_THREADS : NTHREADS;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) {
+    set_error(std::string("tc mode kernel smem attribute: ") + cudaGetErrorString(e));
+    return PHIKRON_ECUDA;
   }
   launch_begin(KC_TC_MODE, st);
-  kern<<<grid, NTHREADS, sm, st>>>(P, status);
+  kern<<<grid, threads, sm, st>>>(P, status);
   launch_end(st);
   PK_CHECK_LAUNCH();
   return PHIKRON_OK;
 }
 
 template <int KS, int SUB>
-int launch_ks(const GPass& P, bool in_f64, bool trans, int grid, int* status, cudaStream_t st) {
+int launch_ks(const GPass& P, bool in_f64, bool trans, int grid, bool ws, int* status, cudaStream_t st) {
   if (in_f64)
-    return trans ? launch_one<KS, SUB, true, true>(P, grid, status, st) : launch_one<KS, SUB, true, false>(P, grid, status, st);
-  return trans ? launch_one<KS, SUB, false, true>(P, grid, status, st) : launch_one<KS, SUB, false, false>(P, grid, status, st);
+    return trans ? launch_one<KS, SUB, true, true>(P, grid, ws, status, st)
+                 : launch_one<KS, SUB, true, false>(P, grid, ws, status, st);
+  return trans ? launch_one<KS, SUB, false, true>(P, grid, ws, status, st)
+               : launch_one<KS, SUB, false, false>(P, grid, ws, status, st);
 }
 
 int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) {
@@ -606,14 +1050,14 @@ int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) 
   const int grid = (int)std::min<long long>(P.total_tiles, S.grid);
   if (S.sub == 1) {
     switch (S.slices) {
-      case 3: return launch_ks<3, 1>(P, S.in_f64, S.trans, grid, status, st);
-      case 4: return launch_ks<4, 1>(P, S.in_f64, S.trans, grid, status, st);
-      case 5: return launch_ks<5, 1>(P, S.in_f64, S.trans, grid, status, st);
-      case 6: return launch_ks<6, 1>(P, S.in_f64, S.trans, grid, status, st);
+      case 3: return launch_ks<3, 1>(P, S.in_f64, S.trans, grid, S.ws, status, st);
+      case 4: return launch_ks<4, 1>(P, S.in_f64, S.trans, grid, S.ws, status, st);
+      case 5: return launch_ks<5, 1>(P, S.in_f64, S.trans, grid, S.ws, status, st);
+      case 6: return launch_ks<6, 1>(P, S.in_f64, S.trans, grid, S.ws, status, st);
       default: break;
     }
   } else if (S.sub == 2 && S.slices == 3) {
-    return launch_ks<3, 2>(P, S.in_f64, S.trans, grid, status, st);
+    return launch_ks<3, 2>(P, S.in_f64, S.trans, grid, S.ws, status, st);
   }
   set_error("tc mode pass: unsupported (slices, sub-chunks) combination");
   return PHIKRON_EINVAL;

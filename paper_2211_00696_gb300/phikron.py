@@ -56,7 +56,7 @@ KERNEL_CLASSES = ("gemm_f64", "weighted_sum", "squaring", "tc_mode", "convert", 
 class BatchInfo(C.Structure):
     _fields_ = [("units", C.c_int), ("launches", C.c_int), ("mode_jobs", C.c_longlong), ("graph", C.c_int),
                 ("k_chunk", C.c_int), ("big_first", C.c_int), ("grid", C.c_int), ("candidates", C.c_int),
-                ("tuned", C.c_int), ("best_ms", C.c_double), ("device_bytes", C.c_size_t)]
+                ("tuned", C.c_int), ("best_ms", C.c_double), ("device_bytes", C.c_size_t), ("ws_kernel", C.c_int)]
 
 _lib = None
 
