@@ -52,9 +52,12 @@ extern "C" {
                                          accumulation in TMEM); state, node weights and the
                                          squaring recurrence in float-float (~48 bits);
                                          1D exponentials in float64.  Needs every n[d] a
-                                         multiple of 16 in 16..256, l_max <= 8, m <= 64.
-                                         For n[d] > 128 the second digit level of that mode
-                                         rounds at ~2^-32 relative (FP32-class products).   */
+                                         multiple of 16 in 16..4096, l_max <= 8, m <= 64.
+                                         The FP32 accumulation of a digit level is exact
+                                         while its partial sums stay below 2^24 units; for
+                                         long contractions (n[d] in the hundreds and more)
+                                         the leading levels round at ~2^-24 of their partial
+                                         sums, which bounds the accuracy of that mode.      */
 
 #define PHIKRON_SELECT_PAPER      0   /* (s, m) from Algorithm 5                            */
 #define PHIKRON_SELECT_MLP        1   /* (s, m) from the learned selector, checked a posteriori,
@@ -91,7 +94,7 @@ typedef struct phikron_plan_s* phikron_plan_t;
  * beta) (Algorithm 5); Gauss-Legendre nodes x_k and weights w_k on [0,1]; the node
  * weights c_{j,k} = w_k x_k^{j-1}/(j-1)!; and on the device every 1D exponential the
  * apply needs: E_{k,d} = exp((1-x_k) 2^{-s} M^d) and G_{t,d} = exp(2^{t-s} M^d),
- * t = 0..s, with M^d = -tau*A^d (batched float64 Pade [13/13] scaling and squaring).
+ * t = 0..s, with M^d = -tau*A^d (batched float64 Taylor scaling and squaring).
  *
  *   out    : receives the plan (owned by the library; free with phikron_destroy).
  *   dims   : 2 or 3.
@@ -289,9 +292,10 @@ int phikron_clenshaw_curtis(int n, double* x, double* w);
  */
 
 /* E[b] = exp(scale[b] * A[b]) for count matrices of size n x n (row-major, contiguous),
- * float64 Pade scaling and squaring (Higham 2005).  scale is a HOST array of count
- * doubles; norms1 is a HOST array with ||A[b]||_1 (used to pick degree and scaling
- * without a device round trip).  workspace: DEVICE, at least
+ * float64 scaling and squaring with the degree-18 Taylor polynomial (Paterson-Stockmeyer,
+ * GEMMs only; ||2^-s scale A||_1 <= 1 keeps the truncation below the float64 unit
+ * roundoff).  scale is a HOST array of count doubles; norms1 is a HOST array with
+ * ||A[b]||_1 (used to pick the scaling without a device round trip).  workspace: DEVICE, at least
  * phikron_expm_workspace_bytes(count, n) bytes. */
 size_t phikron_expm_workspace_bytes(int count, int n);
 int phikron_expm_batched(int count, int n, const double* A, const double* scale,

@@ -1,20 +1,20 @@
-// K1: batched float64 matrix exponential exp(c_b * A_b) by Pade [13/13] scaling and
-// squaring (Higham, SIAM J. Matrix Anal. Appl. 26 (2005), the published method).
+// K1: batched float64 matrix exponential exp(c_b * A_b) by Taylor scaling and squaring, with
+// the degree-18 Taylor polynomial evaluated by the Paterson-Stockmeyer scheme (GEMMs only).
 //
 // The paper needs 1D exponentials exp((1 - x_k) 2^{-s} M^d) at every quadrature node and
 // exp(2^{t-s} M^d) for the squaring steps (Algorithm 6; Eq. (7)-(8)), and leaves the
 // algorithm for them unspecified (MATLAB's expm).  Here:
-//   * Pade coefficients come from the closed form b_j = (2m-j)! m! / ((2m)! j! (m-j)!),
-//     evaluated by the ratio b_j/b_{j-1} = (m-j+1)/((2m-j+1) j) with b_0 = 1 (any common
-//     factor cancels in (V-U)^{-1}(V+U)).
-//   * theta_13 = 5.371920351148152 is the published backward-error threshold for m = 13.
-//   * Degree 13 for every matrix and a squaring count per matrix,
-//     s_b = max(0, ceil(log2(eta_b/theta_13))), where eta_b = |c_b| ||A_b||_1 comes from the
-//     host, so no device round trip is needed to choose them.  The batch is processed in
-//     descending order of s_b, so the matrices still being squared at step t form a prefix
-//     and each squaring is one batched GEMM over that prefix.
-//   * Every contraction runs on the FP64 GEMM; (V-U) R = V+U is solved with one CTA per
-//     matrix by Gaussian elimination with partial pivoting.
+//   * B = 2^{-s_b} c_b A_b with s_b = max(0, ceil(log2 ||c_b A_b||_1)), so ||B||_1 <= 1.  The
+//     Taylor remainder of degree 18 then obeys ||R(B)|| <= e ||B||^19/19! <= 2.3e-17, and
+//     ||e^B|| >= e^{-1}, so the truncation is below the float64 unit roundoff relative to the
+//     result; the s_b squarings follow.
+//   * T18(B) = C0 + B4 (C1 + B4 (C2 + B4 (C3 + B4 C4))) with C_j = sum_{i<4} B^i/(4j+i)!
+//     (C4 = I/16! + B/17! + B^2/18!): B^2, B^3, B^4 and four Horner products, 7 GEMMs.
+//   * s_b comes from the host-side norm, so no device round trip is needed.  The batch is
+//     processed in descending order of s_b, so the matrices still being squared at step t
+//     form a prefix and each squaring is one batched GEMM over that prefix.
+//   * There is no linear solve (a Pade denominator solve is sequential in n and, with one CTA
+//     per matrix, dominated plan time for n >= 1024).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -25,7 +25,8 @@ namespace phikron {
 
 namespace {
 
-constexpr double kTheta13 = 5.371920351148152;
+constexpr double kTheta = 1.0;  // ||B||_1 bound for the degree-18 Taylor polynomial
+constexpr int kDeg = 18;
 constexpr int kChunk = 256;
 
 struct ScaleArgs {
@@ -64,95 +65,6 @@ __global__ void lincomb_kernel(double* __restrict__ out, const double* __restric
   }
 }
 
-// P <- V - U, Q <- V + U (batched)
-__global__ void pq_kernel(const double* __restrict__ U, const double* __restrict__ V,
-                          double* __restrict__ P, double* __restrict__ Q, long long total) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const double u = U[e], v = V[e];
-    P[e] = v - u;
-    Q[e] = v + u;
-  }
-}
-
-// Solve P X = Q in place (X overwrites Q) for one n x n system per CTA, Gaussian
-// elimination with partial pivoting followed by back substitution.
-__global__ void __launch_bounds__(256) lu_solve_kernel(double* __restrict__ Pall,
-                                                       double* __restrict__ Qall, int n) {
-  double* P = Pall + (long long)blockIdx.x * n * n;
-  double* Q = Qall + (long long)blockIdx.x * n * n;
-  __shared__ double red_v[256];
-  __shared__ int red_i[256];
-  __shared__ int piv_s;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = k;
-    for (int i = k + tid; i < n; i += nt) {
-      const double a = fabs(P[(long long)i * n + k]);
-      if (a > best) { best = a; bi = i; }
-    }
-    red_v[tid] = best;
-    red_i[tid] = bi;
-    __syncthreads();
-    for (int o = nt / 2; o > 0; o >>= 1) {
-      if (tid < o) {
-        if (red_v[tid + o] > red_v[tid] ||
-            (red_v[tid + o] == red_v[tid] && red_i[tid + o] < red_i[tid])) {
-          red_v[tid] = red_v[tid + o];
-          red_i[tid] = red_i[tid + o];
-        }
-      }
-      __syncthreads();
-    }
-    if (tid == 0) piv_s = red_i[0];
-    __syncthreads();
-    const int piv = piv_s;
-    if (piv != k) {
-      for (int j = tid; j < n; j += nt) {
-        double t = P[(long long)k * n + j];
-        P[(long long)k * n + j] = P[(long long)piv * n + j];
-        P[(long long)piv * n + j] = t;
-        t = Q[(long long)k * n + j];
-        Q[(long long)k * n + j] = Q[(long long)piv * n + j];
-        Q[(long long)piv * n + j] = t;
-      }
-    }
-    __syncthreads();
-    const double inv = 1.0 / P[(long long)k * n + k];
-    for (int i = k + 1 + tid; i < n; i += nt) P[(long long)i * n + k] *= inv;
-    __syncthreads();
-    const int rows = n - k - 1;
-    const int wp = n - k - 1;  // P columns k+1..n-1
-    const long long work = (long long)rows * (wp + n);
-    for (long long e = tid; e < work; e += nt) {
-      const int r = static_cast<int>(e / (wp + n));
-      const int c = static_cast<int>(e % (wp + n));
-      const int i = k + 1 + r;
-      const double l = P[(long long)i * n + k];
-      if (c < wp) {
-        const int j = k + 1 + c;
-        P[(long long)i * n + j] -= l * P[(long long)k * n + j];
-      } else {
-        const int j = c - wp;
-        Q[(long long)i * n + j] -= l * Q[(long long)k * n + j];
-      }
-    }
-    __syncthreads();
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    const double inv = 1.0 / P[(long long)k * n + k];
-    for (int j = tid; j < n; j += nt) Q[(long long)k * n + j] *= inv;
-    __syncthreads();
-    const long long work = (long long)k * n;
-    for (long long e = tid; e < work; e += nt) {
-      const int i = static_cast<int>(e / n), j = static_cast<int>(e % n);
-      Q[(long long)i * n + j] -= P[(long long)i * n + k] * Q[(long long)k * n + j];
-    }
-    __syncthreads();
-  }
-}
-
 int ew_grid(long long total) {
   long long b = (total + 255) / 256;
   return static_cast<int>(std::max(1LL, std::min(b, 152LL * 16)));
@@ -174,7 +86,7 @@ int bgemm(const double* A, const double* B, double* C, int count, int n, double 
 }  // namespace
 
 size_t expm_workspace_bytes(int count, int n) {
-  return (size_t)9 * (size_t)count * (size_t)n * (size_t)n * sizeof(double);
+  return (size_t)6 * (size_t)count * (size_t)n * (size_t)n * sizeof(double);
 }
 
 int expm_batched(int count, int n, const double* A, const double* scale_host,
@@ -192,29 +104,26 @@ int expm_batched(int count, int n, const double* A, const double* scale_host,
       set_error("expm_batched: non-finite norm or scale");
       return PHIKRON_EINVAL;
     }
-    sp[b] = (e > kTheta13) ? static_cast<int>(std::ceil(std::log2(e / kTheta13))) : 0;
+    sp[b] = (e > kTheta) ? static_cast<int>(std::ceil(std::log2(e / kTheta))) : 0;
     sp_max = std::max(sp_max, sp[b]);
     order[b] = b;
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sp[a] > sp[b]; });
 
-  // Pade [13/13] coefficients b_0..b_13 with b_0 = 1
-  double bc[14];
-  bc[0] = 1.0;
-  for (int j = 1; j <= 13; ++j) bc[j] = bc[j - 1] * (13.0 - j + 1.0) / ((26.0 - j + 1.0) * j);
+  // 1/k!, k = 0..18
+  double inv[kDeg + 1];
+  inv[0] = 1.0;
+  for (int k = 1; k <= kDeg; ++k) inv[k] = inv[k - 1] / k;
 
   const long long nn = (long long)n * n;
   const long long total = nn * count;
   double* w = static_cast<double*>(ws);
   double* B = w;
   double* B2 = w + total;
-  double* B4 = w + 2 * total;
-  double* B6 = w + 3 * total;
-  double* T1 = w + 4 * total;
-  double* U = w + 5 * total;
-  double* V = w + 6 * total;
-  double* P = w + 7 * total;
-  double* Q = w + 8 * total;
+  double* B3 = w + 2 * total;
+  double* B4 = w + 3 * total;
+  double* H = w + 4 * total;
+  double* T1 = w + 5 * total;
 
   for (int b0 = 0; b0 < count; b0 += kChunk) {
     const int c = std::min(kChunk, count - b0);
@@ -230,28 +139,24 @@ int expm_batched(int count, int n, const double* A, const double* scale_host,
   }
   const int g = ew_grid(total);
   PK_RET(bgemm(B, B, B2, count, n, 0.0, st));
+  PK_RET(bgemm(B2, B, B3, count, n, 0.0, st));
   PK_RET(bgemm(B2, B2, B4, count, n, 0.0, st));
-  PK_RET(bgemm(B4, B2, B6, count, n, 0.0, st));
-  // U = B * (B6*(b13 B6 + b11 B4 + b9 B2) + b7 B6 + b5 B4 + b3 B2 + b1 I)
-  lincomb_kernel<<<g, 256, 0, st>>>(T1, B6, B4, B2, nullptr, bc[13], bc[11], bc[9], 0.0, 0.0, n, total);
+  // H = C4 = I/16! + B/17! + B^2/18!
+  lincomb_kernel<<<g, 256, 0, st>>>(H, B, B2, nullptr, nullptr, inv[17], inv[18], 0.0, 0.0, inv[16], n, total);
   PK_CHECK_LAUNCH();
-  lincomb_kernel<<<g, 256, 0, st>>>(V, B6, B4, B2, nullptr, bc[7], bc[5], bc[3], 0.0, bc[1], n, total);
-  PK_CHECK_LAUNCH();
-  PK_RET(bgemm(B6, T1, V, count, n, 1.0, st));  // V holds the bracket for U
-  PK_RET(bgemm(B, V, U, count, n, 0.0, st));
-  // V = B6*(b12 B6 + b10 B4 + b8 B2) + b6 B6 + b4 B4 + b2 B2 + b0 I
-  lincomb_kernel<<<g, 256, 0, st>>>(T1, B6, B4, B2, nullptr, bc[12], bc[10], bc[8], 0.0, 0.0, n, total);
-  PK_CHECK_LAUNCH();
-  lincomb_kernel<<<g, 256, 0, st>>>(V, B6, B4, B2, nullptr, bc[6], bc[4], bc[2], 0.0, bc[0], n, total);
-  PK_CHECK_LAUNCH();
-  PK_RET(bgemm(B6, T1, V, count, n, 1.0, st));
-  pq_kernel<<<g, 256, 0, st>>>(U, V, P, Q, total);
-  PK_CHECK_LAUNCH();
-  lu_solve_kernel<<<count, 256, 0, st>>>(P, Q, n);
-  PK_CHECK_LAUNCH();
+  // H <- C_j + B4 H for j = 3, 2, 1, 0 (C_j preloaded into the destination, beta = 1)
+  double* cur = H;
+  double* nxt = T1;
+  for (int j = 3; j >= 0; --j) {
+    lincomb_kernel<<<g, 256, 0, st>>>(nxt, B, B2, B3, nullptr, inv[4 * j + 1], inv[4 * j + 2], inv[4 * j + 3], 0.0,
+                                      inv[4 * j], n, total);
+    PK_CHECK_LAUNCH();
+    PK_RET(bgemm(B4, cur, nxt, count, n, 1.0, st));
+    std::swap(cur, nxt);
+  }
   // undo the scaling: R <- R^2, s_b times; matrices with s_b > t form the prefix of length
   // cnt(t), squared by one batched GEMM while the others stay where they are
-  double* bufs[2] = {Q, T1};
+  double* bufs[2] = {cur, nxt};
   for (int t = 0; t < sp_max; ++t) {
     int cnt = 0;
     while (cnt < count && sp[order[cnt]] > t) ++cnt;

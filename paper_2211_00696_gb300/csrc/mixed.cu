@@ -290,8 +290,8 @@ size_t sliced_bytes(int n, int slices) {
   return (size_t)nhalves * nchunks * slices * SLICE_BYTES;
 }
 
-// E (n x n, n <= 256) -> [half][chunk32][slice][128 rows x 32 cols core-matrix layout] with
-// rows 128*half .. +127 of E in each half; rexp[half*128 + i] = f with max_k |E[row][k]| < 2^f.
+// E (n x n) -> [row block][chunk32][slice][128 rows x 32 cols core-matrix layout] with rows
+// 128*b .. 128*b+127 of E in block b; rexp[b*128 + i] = f with max_k |E[row][k]| < 2^f.
 // Digits are those of |E| * 2^{64-f} rounded to nearest at digit `slices`.
 void slice_matrix_host(const double* E, int n, int slices, uint8_t* out, int* rexp) {
   const int nchunks = (n + KC - 1) / KC;
@@ -364,8 +364,8 @@ int precision_setup(Plan& P) {
     return PHIKRON_ENOTSUP;
   }
   for (int d = 0; d < P.dims; ++d) {
-    if (P.n[d] < 16 || P.n[d] > 256 || P.n[d] % 16 != 0) {
-      set_error("mixed path: every n[d] must be a multiple of 16 in 16..256");
+    if (P.n[d] < 16 || P.n[d] > 4096 || P.n[d] % 16 != 0) {
+      set_error("mixed path: every n[d] must be a multiple of 16 in 16..4096");
       return PHIKRON_ENOTSUP;
     }
   }

@@ -13,14 +13,14 @@ namespace phikron {
 struct GJob {
   const void* in;          // float64 (pass shape in_f64) or float2 (hi, lo) vector
   const int* in_exp;       // e with |in| < 2^e for the whole vector
-  const uint8_t* eslices;  // E as [half][chunk32][slice][128 rows x 32 K bf16 core-matrix layout]
-  const int* rexp;         // [half][128] row exponents f_i of E (|E[i][k]| < 2^{f_i})
+  const uint8_t* eslices;  // E as [row block][chunk32][slice][128 rows x 32 K bf16 core-matrix layout]
+  const int* rexp;         // [row block][128] row exponents f_i of E (|E[i][k]| < 2^{f_i})
   void* out;               // float2 or float64 (out_f64)
   int* out_exp;            // receives the max exponent of out (atomicMax), or null
   long long R, B0;         // product of faster / slower axes than the contracted one
   long long tile_begin;    // first tile of this job in its pass
   long long tab_off_in, tab_off_out;  // byte offsets when in_tab / out_tab >= 0
-  int n;                   // contracted size (E is n x n), multiple of 16, <= 256
+  int n;                   // contracted size (E is n x n), multiple of 16, <= 4096
   int out_f64;
   int in_tab, out_tab;     // pointer-table entries, or -1
 };

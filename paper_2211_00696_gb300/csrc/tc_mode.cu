@@ -270,7 +270,7 @@ struct Raw {
 
 struct TileCtx {
   int job;
-  int half;            // which 128-row half of E (n > 128)
+  int rb;            // which 128-row block of E (n > 128)
   int n, nsub;         // contracted size, number of 32-wide K sub-chunks
   long long R, B0;
   long long b0, r0, row0;
@@ -301,9 +301,9 @@ __device__ __forceinline__ TileCtx tile_ctx(const GPass& P, long long tile, int 
   t.B0 = J.B0;
   const long long tj = tile - J.tile_begin;
   const long long rtiles = TRANS ? (J.R + 127) / 128 : 1;
-  const long long per_half = TRANS ? J.B0 * rtiles : (J.B0 + 127) / 128;
-  t.half = (int)(tj / per_half);
-  const long long th = tj % per_half;
+  const long long per_rb = TRANS ? J.B0 * rtiles : (J.B0 + 127) / 128;
+  t.rb = (int)(tj / per_rb);
+  const long long th = tj % per_rb;
   t.b0 = t.r0 = t.row0 = 0;
   if (TRANS) {
     t.b0 = th / rtiles;
@@ -335,7 +335,7 @@ __device__ __forceinline__ void load_raw(const TileCtx& t, int sub, int kq, Raw<
   }
 }
 
-// One tile = 128 operand rows (r for TRANS, X rows for NORMAL) x one 128-row half of E,
+// One tile = 128 operand rows (r for TRANS, X rows for NORMAL) x one 128-row block of E,
 // accumulated over the full contraction K = n in chunks of 32*SUB.
 template <int KS, int SUB, bool IN_F64, bool TRANS>
 __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant__ GPass P, int* status) {
@@ -383,10 +383,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
     const GJob& J = P.jobs[T.job];
     const int n = T.n;
     const int nchunks = (T.nsub + SUB - 1) / SUB;
-    const int nrows_e = min(128, n - 128 * T.half);   // E rows in this half
-    const uint8_t* ebase = J.eslices + (size_t)T.half * (size_t)T.nsub * KS * SLICE_BYTES;
+    const int nrows_e = min(128, n - 128 * T.rb);   // E rows in this row block
+    const uint8_t* ebase = J.eslices + (size_t)T.rb * (size_t)T.nsub * KS * SLICE_BYTES;
     if (tid < 128) {
-      const int E = T.eX + ((tid < nrows_e) ? J.rexp[T.half * 128 + tid] : 0);
+      const int E = T.eX + ((tid < nrows_e) ? J.rexp[T.rb * 128 + tid] : 0);
       scale_s[tid] = pow2f(E);
     }
     const uint32_t idesc = TRANS ? make_idesc(128, nrows_e) : make_idesc(128, 128);
@@ -534,14 +534,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
           float sc;
           if (TRANS) {
             il = col;
-            i = 128 * T.half + il;
+            i = 128 * T.rb + il;
             const long long g = T.r0 + lrow;
             ok = (il < nrows_e) && (g < T.R);
             oidx = out_base + (long long)i * T.R + g;
             sc = scale_s[il];
           } else {
             il = lrow;
-            i = 128 * T.half + il;
+            i = 128 * T.rb + il;
             const long long g = T.row0 + col;
             ok = (il < nrows_e) && (g < T.B0);
             oidx = g * (long long)n + i;
@@ -611,13 +611,13 @@ constexpr int WS_SLOT_READERS = WS_PROD + 1 + WS_EPI;
 struct WsSlot {
   const void* in;
   void* out;
-  const uint8_t* ebase;  // E slices of the tile's 128-row half
-  const int* rexp;       // row exponents of that half
+  const uint8_t* ebase;  // E slices of the tile's 128-row block
+  const int* rexp;       // row exponents of that block
   int* out_exp;
   long long R, B0;
   long long base;        // TRANS: b0 * n * R (first element of the tile's slab); NORMAL: 0
   long long g0;          // first fiber of the tile: r0 (TRANS) or row0 (NORMAL)
-  int n, nsub, half, eX, nrows_e, out_f64;
+  int n, nsub, rb, eX, nrows_e, out_f64;
 };
 
 // shared-memory layout after the two stages
@@ -839,10 +839,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       uint32_t mx = 0;   // largest |hi| bit pattern stored
       if (TRANS) {
-        // TMEM lane = fiber r, column = output row i of this half; stores coalesce over lanes
+        // TMEM lane = fiber r, column = output row i of this row block; stores coalesce over lanes
         const long long g = S.g0 + et;
         const bool vg = g < S.R;
-        const long long o0 = S.base + (long long)(128 * S.half) * S.R + g;
+        const long long o0 = S.base + (long long)(128 * S.rb) * S.R + g;
         for (int cc = 0; cc < S.nrows_e; cc += 16) {
           float d2[16], d3[16], d4[16], d5[16];
           tmem_ld16(lane_base + (uint32_t)cc, d2);
@@ -868,11 +868,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
           }
         }
       } else {
-        // TMEM lane = output row i of this half, column = fiber; stores coalesce over lanes
+        // TMEM lane = output row i of this row block, column = fiber; stores coalesce over lanes
         const bool vi = et < S.nrows_e;
         const int ncols = (int)min(128LL, S.B0 - S.g0);
         const float sc = scale_s[et];
-        const long long o0 = S.g0 * (long long)S.n + 128 * S.half + et;
+        const long long o0 = S.g0 * (long long)S.n + 128 * S.rb + et;
         for (int cc = 0; cc < ncols; cc += 16) {
           float d2[16], d3[16], d4[16], d5[16];
           tmem_ld16(lane_base + (uint32_t)cc, d2);
@@ -976,15 +976,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       const GJob& J = P.jobs[job];
       const long long tj = tile - J.tile_begin;
       const long long rtiles = TRANS ? (J.R + 127) / 128 : 1;
-      const long long per_half = TRANS ? J.B0 * rtiles : (J.B0 + 127) / 128;
-      const int half = (int)(tj / per_half);
-      const long long th = tj % per_half;
+      const long long per_rb = TRANS ? J.B0 * rtiles : (J.B0 + 127) / 128;
+      const int rb = (int)(tj / per_rb);
+      const long long th = tj % per_rb;
       WsSlot& S = slots[q];
       S.in = (J.in_tab >= 0) ? (const void*)((const char*)P.ptrtab[J.in_tab] + J.tab_off_in) : J.in;
       S.out = (J.out_tab >= 0) ? (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out) : J.out;
       const int nsub = (J.n + 31) / 32;
-      S.ebase = J.eslices + (size_t)half * (size_t)nsub * KS * SLICE_BYTES;
-      S.rexp = J.rexp + 128 * half;
+      S.ebase = J.eslices + (size_t)rb * (size_t)nsub * KS * SLICE_BYTES;
+      S.rexp = J.rexp + 128 * rb;
       S.out_exp = J.out_exp;
       S.R = J.R;
       S.B0 = J.B0;
@@ -992,10 +992,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       S.g0 = TRANS ? (th % rtiles) * 128 : th * 128;
       S.n = J.n;
       S.nsub = nsub;
-      S.half = half;
+      S.rb = rb;
       const int eX = *J.in_exp;
       S.eX = eX < -600 ? 0 : eX;  // all-zero input
-      S.nrows_e = min(128, J.n - 128 * half);
+      S.nrows_e = min(128, J.n - 128 * rb);
       S.out_f64 = J.out_f64;
       mbar_arrive(smem_u32(&slot_full[q]));
     }

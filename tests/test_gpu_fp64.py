@@ -39,9 +39,9 @@ def test_expm_batched_matches_scipy(n):
     E = _pk().expm_batched(_dev(A), scales).cpu().numpy()
     for b, c in enumerate(scales):
         ref = scipy.linalg.expm(c * A[b])
-        # Pade [13/13] error ~u; each of the s_b squarings can add a few u (s_b from Higham
-        # 2005's theta_13 rule; the same algorithm in numpy shows ~1.8e-13 at s_b = 9)
-        sb = max(0, int(np.ceil(np.log2(abs(c) * np.abs(A[b]).sum(0).max() / 5.371920351148152))))
+        # degree-18 Taylor truncation < u at ||B||_1 <= 1; each of the s_b squarings can add a
+        # few u (s_b = ceil(log2 ||cA||_1); scaling and squaring in numpy shows ~1.8e-13 at 9)
+        sb = max(0, int(np.ceil(np.log2(abs(c) * np.abs(A[b]).sum(0).max()))))
         tol = 2e-14 * (5 + 5 * sb)
         assert np.linalg.norm(E[b] - ref) <= tol * max(1.0, np.linalg.norm(ref)), (b, c, sb)
 

@@ -121,3 +121,29 @@ def test_mixed_rejects_unsupported_sizes():
     pk = _pk()
     with pytest.raises(pk.PhikronError):
         pk.Plan([W.laplacian_factor(20), W.laplacian_factor(32)], 1e-3, 2, 1e-8, precision=pk.PREC_OZAKI_BF16)
+    with pytest.raises(pk.PhikronError):     # above the 4096 limit of the mixed path
+        pk.Plan([W.laplacian_factor(4112), W.laplacian_factor(16)], 1e-6, 1, 1e-8, precision=pk.PREC_OZAKI_BF16)
+
+
+@pytest.mark.parametrize("n,prec,tol", [(512, "mixed", 1e-10), (2048, "mixed", 1e-6), (2048, "mixed", 1e-10),
+                                        (2048, "fp64", 1e-10)])
+def test_large_n_periodic_2d_vs_spectral(n, prec, tol):
+    """Long contractions (K = n up to 2048, 64 K-chunks, 16 E row blocks) on the 2D periodic
+    diffusion operator of the Allen-Cahn workload (eps^2 = 1e-4, tau = 1e-2, phi_0 and phi_1)
+    against the DFT-diagonalised oracle; the gate is the plan tolerance."""
+    import time
+    pk = _pk()
+    coeff, tau, p = 1e-4, 1e-2, 1
+    fac = [W.periodic_diffusion_factor(n, coeff)] * 2
+    v = W.uniform_vector((n, n), 7)
+    exact = P.phi_spectral_periodic((n, n), [coeff] * 2, tau, v, p)
+    t0 = time.perf_counter()
+    plan = pk.Plan(fac, tau, p, tol, precision=pk.PREC_OZAKI_BF16 if prec == "mixed" else pk.PREC_FP64)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    out = plan.apply(_dev(v)).cpu().numpy()
+    plan.check_status()
+    errs = [P.rel_err_2(out[l], exact[l]) for l in range(p + 1)]
+    print(f"n={n} {prec} tol={tol:g}: plan {plan_s:.2f} s, errors {errs}")
+    assert max(errs) <= tol
+    assert plan_s < 20.0
