@@ -80,6 +80,9 @@ typedef struct phikron_opts {
   int    half_step;   /* OZAKI_BF16 and l_max >= 1: also return phi_l(-tau/2*A) v, l = 0..l_max
                          (the state before the last squaring step of Eq. (29); s >= 1 is then
                          enforced).  Out then holds 2*(l_max+1) vectors: tau first, tau/2 next. */
+  int    skip_phi0;   /* l_max >= 1: do not compute phi_0 (one Kronecker action fewer); the
+                         phi_0 slots of Out (and of the tau/2 block) are left untouched.
+                         Exponential Runge-Kutta stages need phi_1..phi_p only.  Default 0.  */
 } phikron_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -318,6 +321,44 @@ int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const
 long long phikron_noalloc_max_elements(void);
 int phikron_kron_apply_f64_noalloc(int dims, const int* n, const double* const* E, const double* V,
                                    double* Out, void* stream);
+
+/* ------------------------------------------------------------------ exponential integrators
+ * Exponential Runge-Kutta drivers for u' + A u = f(u), A = A^x (+) A^y (+) A^z (Sec. 2,
+ * Eq. (RK), Table RK), each step built from phi-function actions of this library:
+ *   PHIKRON_ERK_EULER : u+ = u + tau phi_1(-tau A)(f(u) - A u)                 (1 action/step)
+ *   PHIKRON_ERK_RK2   : two stages, c2 = 1/2                                    (2 actions/step)
+ *   PHIKRON_ERK_RK3   : three stages, c2 = 1/3, c3 = 2/3                        (5 actions/step)
+ * with D_j = f(U_j) - A u as in Eq. (RK).  One plan per distinct c_j tau (created here with
+ * the given tol and opts, phi_0 skipped; opts.half_step must be 0); A u is applied from the
+ * nonzeros of the 1D factors (CSR per dimension, no dense product).
+ *   nonlinearity : PHIKRON_NONLIN_NONE (f = 0) or PHIKRON_NONLIN_ALLEN_CAHN (f(u) = u - u^3).
+ *   A, n         : HOST, as for phikron_plan (copied).
+ * phikron_erk_step advances U (DEVICE, N float64, in place) by nsteps steps of size tau on
+ * stream (asynchronous).  Errors: PHIKRON_EINVAL for bad arguments, the plan's codes
+ * otherwise; phikron_erk_check_status reports a kernel-side timeout of any plan. */
+#define PHIKRON_ERK_EULER          1
+#define PHIKRON_ERK_RK2            2
+#define PHIKRON_ERK_RK3            3
+#define PHIKRON_NONLIN_NONE        0
+#define PHIKRON_NONLIN_ALLEN_CAHN  1
+
+typedef struct phikron_erk_s* phikron_erk_t;
+
+typedef struct phikron_erk_info {
+  int    method;
+  int    nplans;            /* distinct c_j tau                                            */
+  int    applies_per_step;  /* phi-function actions (right-hand sides) per step            */
+  double c[3];              /* c_j of each plan                                            */
+  int    s[3], m[3];        /* (s, m) of each plan                                         */
+  int    actions[3];        /* Kronecker actions per apply of each plan                    */
+} phikron_erk_info;
+
+int  phikron_erk_create(phikron_erk_t* out, int method, int dims, const double* const* A, const int* n,
+                        double tau, double tol, int nonlinearity, const phikron_opts* opts);
+int  phikron_erk_step(phikron_erk_t erk, double* U, int nsteps, void* stream);
+int  phikron_erk_get_info(phikron_erk_t erk, phikron_erk_info* info);
+int  phikron_erk_check_status(phikron_erk_t erk);
+void phikron_erk_destroy(phikron_erk_t erk);
 
 #ifdef __cplusplus
 }

@@ -3,6 +3,7 @@
 The compute path is the CUDA library libphikron.so (include/phikron.h); this package is
 its Python binding (``phikron``) and build script (``build``).
 """
-from .phikron import (Plan, Batch, PhikronError, lib, log_quaderr, quadnodes, setup_quadrature,  # noqa: F401
+from .phikron import (Plan, Batch, Integrator, PhikronError, lib, log_quaderr, quadnodes, setup_quadrature,  # noqa: F401
                       gauss_legendre, clenshaw_curtis, expm_batched, kron_apply_f64,
-                      PREC_FP64, PREC_OZAKI_BF16, QUAD_GAUSS, QUAD_CC)
+                      PREC_FP64, PREC_OZAKI_BF16, QUAD_GAUSS, QUAD_CC,
+                      ERK_EULER, ERK_RK2, ERK_RK3, NONLIN_NONE, NONLIN_ALLEN_CAHN)

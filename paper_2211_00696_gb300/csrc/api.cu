@@ -370,11 +370,13 @@ int apply_f64(Plan& P, const double* V, double* Out, cudaStream_t st) {
     return kron_chain_f64(P, V, 0, 1, m, 0, P.dW1, P.dW2, Out, st);
   }
   // node phase: m node actions + phi_0 in one batched chain (v shared: stride 0)
-  PK_RET(kron_chain_f64(P, V, 0, m + 1, 0, 1, P.dW1, P.dW2,
+  const bool phi0 = !P.opts.skip_phi0;
+  PK_RET(kron_chain_f64(P, V, 0, m + (phi0 ? 1 : 0), 0, 1, P.dW1, P.dW2,
                         (P.dims % 2 == 1) ? P.dW1 : P.dW2, st));
   const double* T = (P.dims % 2 == 1) ? P.dW1 : P.dW2;
   // the chain's last destination is the buffer given; use a dedicated one to avoid aliasing
-  PK_TRY_CUDA(cudaMemcpyAsync(Out, T + (size_t)m * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  if (phi0)
+    PK_TRY_CUDA(cudaMemcpyAsync(Out, T + (size_t)m * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   double* Y = (s == 0) ? Out + N : P.dY;
   PK_RET(weighted_sum_f64(T, N, P.dCoef, p, m, N, Y, N, st));
   double* Yn = P.dYn;
@@ -411,6 +413,7 @@ void phikron_opts_default(phikron_opts* o) {
   o->max_rhs = 1;
   o->slices = 0;
   o->half_step = 0;
+  o->skip_phi0 = 0;
 }
 
 const char* phikron_last_error(void) { return g_err.c_str(); }
@@ -446,6 +449,10 @@ int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const in
   }
   if (o.half_step && l_max == 0) {
     set_error("phikron_plan: half_step needs l_max >= 1");
+    return PHIKRON_EINVAL;
+  }
+  if (o.skip_phi0 && l_max == 0) {
+    set_error("phikron_plan: skip_phi0 needs l_max >= 1");
     return PHIKRON_EINVAL;
   }
   if (o.selector != PHIKRON_SELECT_PAPER && o.selector != PHIKRON_SELECT_MLP) {
@@ -517,7 +524,7 @@ int phikron_plan_info(phikron_plan_t plan, phikron_info* info) {
   info->s = P.s;
   info->m = P.m;
   info->cost = P.cost;
-  info->actions = (P.p == 0) ? 1 : P.m + P.s * P.p + 1;
+  info->actions = (P.p == 0) ? 1 : P.m + P.s * P.p + (P.opts.skip_phi0 ? 0 : 1);
   info->alpha = P.alpha;
   info->log10_bound = P.log10_bound;
   info->precision = P.opts.precision;

@@ -705,8 +705,9 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       us[u].next += P.m;
       for (int k = 0; k < P.m; ++k)
         vs.push_back(CV{u, k, nullptr, us[u].vslot, true, k, T[u] + (size_t)k * P.N, false, 0, false, tslot[u] + k});
-      vs.push_back(CV{u, P.m, nullptr, us[u].vslot, true, P.m, nullptr, true, 0, true, -1});
-      if (cfg.half)
+      if (!P.opts.skip_phi0)
+        vs.push_back(CV{u, P.m, nullptr, us[u].vslot, true, P.m, nullptr, true, 0, true, -1});
+      if (cfg.half && !P.opts.skip_phi0)
         vs.push_back(CV{u, P.m + P.s, nullptr, us[u].vslot, true, P.m + 1, nullptr, true,
                         (long long)(p + 1) * P.N * 8, true, -1});
     }

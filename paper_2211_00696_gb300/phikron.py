@@ -35,7 +35,7 @@ class Opts(C.Structure):
     _fields_ = [("quad", C.c_int), ("precision", C.c_int), ("selector", C.c_int),
                 ("force_s", C.c_int), ("force_m", C.c_int), ("alpha", C.c_double),
                 ("beta", C.c_double), ("device", C.c_int), ("max_rhs", C.c_int), ("slices", C.c_int),
-                ("half_step", C.c_int)]
+                ("half_step", C.c_int), ("skip_phi0", C.c_int)]
 
 
 class Info(C.Structure):
@@ -51,6 +51,11 @@ class Profile(C.Structure):
 
 
 KERNEL_CLASSES = ("gemm_f64", "weighted_sum", "squaring", "tc_mode", "convert", "other")
+
+
+class ErkInfo(C.Structure):
+    _fields_ = [("method", C.c_int), ("nplans", C.c_int), ("applies_per_step", C.c_int),
+                ("c", C.c_double * 3), ("s", C.c_int * 3), ("m", C.c_int * 3), ("actions", C.c_int * 3)]
 
 
 class BatchInfo(C.Structure):
@@ -82,6 +87,12 @@ SIGNATURES = {
     "phikron_batch_get_info": (C.c_int, [C.c_void_p, C.POINTER(BatchInfo)]),
     "phikron_batch_check_status": (C.c_int, [C.c_void_p]),
     "phikron_batch_destroy": (None, [C.c_void_p]),
+    "phikron_erk_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(_DP), C.POINTER(C.c_int),
+                                     C.c_double, C.c_double, C.c_int, C.POINTER(Opts)]),
+    "phikron_erk_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "phikron_erk_get_info": (C.c_int, [C.c_void_p, C.POINTER(ErkInfo)]),
+    "phikron_erk_check_status": (C.c_int, [C.c_void_p]),
+    "phikron_erk_destroy": (None, [C.c_void_p]),
     "phikron_selector_features": (C.c_int, [C.c_int, _IP, _DP, C.c_int, C.c_double, C.POINTER(C.c_float)]),
     "phikron_selector_criterion": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _DP]),
     "phikron_selector_search": (C.c_int, [C.c_int, _DP, _DP, _IP, _DP, C.c_int, C.c_int, _IP, _IP, _IP]),
@@ -186,7 +197,7 @@ class Plan:
     def __init__(self, factors, tau: float, l_max: int, tol: float, *, precision: int = PREC_FP64,
                  quad: int = QUAD_GAUSS, force_s: int = -1, force_m: int = -1, alpha: float = 0.0,
                  beta: float = 0.0, device: int = -1, max_rhs: int = 1, slices: int = 0,
-                 half_step: bool = False, selector: int = SELECT_PAPER):
+                 half_step: bool = False, selector: int = SELECT_PAPER, skip_phi0: bool = False):
         L = lib()
         self._h = C.c_void_p()
         facs = [np.ascontiguousarray(a, dtype=np.float64) for a in factors]
@@ -201,6 +212,7 @@ class Plan:
         o.quad, o.precision, o.force_s, o.force_m = quad, precision, force_s, force_m
         o.alpha, o.beta, o.device, o.max_rhs, o.slices = alpha, beta, device, max_rhs, slices
         o.half_step = 1 if half_step else 0
+        o.skip_phi0 = 1 if skip_phi0 else 0
         o.selector = selector
         _check(L.phikron_plan(C.byref(self._h), len(facs), ptrs, ns, tau, l_max, tol, C.byref(o)))
         self.shape = tuple(a.shape[0] for a in facs)
@@ -315,6 +327,55 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib().phikron_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+ERK_EULER, ERK_RK2, ERK_RK3 = 1, 2, 3
+NONLIN_NONE, NONLIN_ALLEN_CAHN = 0, 1
+
+
+class Integrator:
+    """phikron_erk_t owner: exponential Euler / RK2 (c2 = 1/2) / RK3 (c2 = 1/3, c3 = 2/3) for
+    u' + A u = f(u), A the Kronecker sum of ``factors``; every phi-action runs in this library."""
+
+    def __init__(self, factors, tau: float, method: int, tol: float, *, nonlinearity: int = NONLIN_ALLEN_CAHN,
+                 precision: int = PREC_FP64, slices: int = 0, device: int = -1):
+        L = lib()
+        facs = [np.ascontiguousarray(a, dtype=np.float64) for a in factors]
+        self._facs = facs
+        ptrs = (_DP * len(facs))(*[_dp(a) for a in facs])
+        ns = (C.c_int * len(facs))(*[a.shape[0] for a in facs])
+        o = Opts()
+        L.phikron_opts_default(C.byref(o))
+        o.precision, o.slices, o.device = precision, slices, device
+        self._h = C.c_void_p()
+        _check(L.phikron_erk_create(C.byref(self._h), method, len(facs), ptrs, ns, tau, tol, nonlinearity,
+                                    C.byref(o)))
+        self.N = int(np.prod([a.shape[0] for a in facs]))
+
+    def step(self, U, nsteps: int = 1, stream=None):
+        """Advances U (CUDA float64 tensor with N elements, updated in place) by nsteps steps."""
+        _check(lib().phikron_erk_step(self._h, U.data_ptr(), nsteps, _stream_ptr(stream)))
+        return U
+
+    def info(self) -> dict:
+        inf = ErkInfo()
+        _check(lib().phikron_erk_get_info(self._h, C.byref(inf)))
+        return {k: (list(getattr(inf, k)) if k in ("c", "s", "m", "actions") else getattr(inf, k))
+                for k, _ in ErkInfo._fields_}
+
+    def check_status(self):
+        _check(lib().phikron_erk_check_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().phikron_erk_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

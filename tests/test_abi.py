@@ -88,3 +88,12 @@ def test_invalid_arguments_return_einval_without_gpu():
         pk.Plan([np.eye(3), np.full((3, 3), np.nan)], 0.1, 2, 1e-10)
     with pytest.raises(pk.PhikronError):
         pk.Plan([np.eye(3), np.eye(3)], 0.1, 2, 0.0)          # tol <= 0
+    # exponential integrators: argument checks run before any device call
+    for bad in (dict(method=4), dict(method=1, tau=0.0), dict(method=2, nonlinearity=7)):
+        kw = dict(tau=1e-2, nonlinearity=pk.NONLIN_ALLEN_CAHN)
+        kw.update(bad)
+        method = kw.pop("method")
+        tau = kw.pop("tau")
+        with pytest.raises(pk.PhikronError) as e:
+            pk.Integrator([np.eye(4), np.eye(4)], tau, method, 1e-10, **kw)
+        assert e.value.code == B.EINVAL
