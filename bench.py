@@ -239,6 +239,54 @@ def run_batched(args):
                       "batch": info}), flush=True)
 
 
+def run_allen_cahn(args):
+    """Semilinear 2D Allen-Cahn u' = eps^2 Lap(u) + u - u^3 on the 2048^2 periodic grid
+    (eps = 0.01, tau = 1e-2, u0 ~ U(-0.05, 0.05) seed 4): exponential Euler and the two-stage
+    method (c2 = 1/2) through the library's integrator, mixed (tol 1e-10) and float64 (tol
+    1e-12), --steps time steps each (default 200); value = unknowns x time steps per second of
+    the mixed run; the final-state difference mixed vs float64 is the accuracy gate (<= 1e-6)."""
+    import torch
+    import paper_2211_00696_gb300 as pk
+    torch.cuda.set_device(0)
+    a, u0 = W.allen_cahn2d()
+    fac = [a, a]
+    N = u0.size
+    nsteps = args.steps if args.steps != 20 else 200
+    st = torch.cuda.current_stream()
+    res = {}
+    for method, mid in (("euler", pk.ERK_EULER), ("rk2", pk.ERK_RK2)):
+        finals = {}
+        for prec, pid, tol in (("mixed", pk.PREC_OZAKI_BF16, 1e-10), ("fp64", pk.PREC_FP64, 1e-12)):
+            it = pk.Integrator(fac, 1e-2, mid, tol, precision=pid)
+            U = torch.from_numpy(u0.copy()).cuda()
+            it.step(U, 1)                   # warm-up (graph instantiation, first launches)
+            U.copy_(torch.from_numpy(u0))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            it.step(U, nsteps)
+            e1.record(st)
+            torch.cuda.synchronize()
+            it.check_status()
+            ms = e0.elapsed_time(e1)
+            info = it.info()
+            it.close()
+            finals[prec] = U.cpu().numpy()
+            res[f"{method}_{prec}"] = {"ms_total": ms, "ms_per_step": ms / nsteps,
+                                       "unknown_steps_per_s": N * nsteps / (ms * 1e-3),
+                                       "plans": {"c": info["c"][:info["nplans"]], "s": info["s"][:info["nplans"]],
+                                                 "m": info["m"][:info["nplans"]]}}
+        d = np.linalg.norm(finals["mixed"] - finals["fp64"]) / np.linalg.norm(finals["fp64"])
+        res[f"{method}_final_rel_diff_mixed_vs_fp64"] = float(d)
+    line = {"metric": "Allen-Cahn 2048^2 exponential integrators, unknowns x steps / s (mixed)",
+            "value": res["euler_mixed"]["unknown_steps_per_s"], "unit": "unknown-steps/s", "steps": nsteps,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "allen_cahn2d_2048_periodic_eps0.01_tau1e-2", "N": N, "time_steps": nsteps},
+            "results": res,
+            "gate_final_rel_diff_le_1e-6": all(res[f"{m}_final_rel_diff_mixed_vs_fp64"] <= 1e-6 for m in ("euler", "rk2"))}
+    print(json.dumps(line), flush=True)
+
+
 def fp64_gpu_compare(prob, V, out_shape, flush, golden, dev, local, steps=3):
     """The same workload on the float64 GPU path (float64 DFMA mode products), timed the same
     way: the comparison the metric names (mixed vs FP64 GPU at the stated accuracy)."""
@@ -414,7 +462,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=list(PRECISIONS))
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--workload", default="convdiff3d", choices=["convdiff3d", "batched"])
+    ap.add_argument("--workload", default="convdiff3d", choices=["convdiff3d", "batched", "allen_cahn"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -422,6 +470,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "allen_cahn":
+        run_allen_cahn(args)
     else:
         run_ours(args)
 
