@@ -42,6 +42,9 @@ extern "C" {
 #define PHIKRON_ENOTCONVERGED  -5  /* planner root finding failed (Theorem 3.2 quartic)         */
 #define PHIKRON_ENOTSUP        -6  /* option combination not built                              */
 
+/* Largest number of Kronecker factors (dimensions) a plan accepts. */
+#define PHIKRON_MAX_DIMS 6
+
 /* ------------------------------------------------------------------ options */
 #define PHIKRON_QUAD_GAUSS        0   /* Gauss-Legendre, Algorithm 1 (Sec. 3.1)            */
 #define PHIKRON_QUAD_CC           1   /* Clenshaw-Curtis nodes with the CC bound            */
@@ -100,7 +103,8 @@ typedef struct phikron_plan_s* phikron_plan_t;
  * t = 0..s, with M^d = -tau*A^d (batched float64 Taylor scaling and squaring).
  *
  *   out    : receives the plan (owned by the library; free with phikron_destroy).
- *   dims   : 2 or 3.
+ *   dims   : 1..PHIKRON_MAX_DIMS (the paper's 2D/3D cases and d > 3, Sec. 2 Remark on
+ *            Kronecker sums of more factors; the learned selector covers dims <= 3).
  *   A      : dims HOST pointers; A[d] is n[d] x n[d], row-major float64.  Copied.
  *   n      : dims sizes, 1 <= n[d] <= 4096.
  *   tau    : time step, finite; phi_l(-tau*A) is computed (tau may be 0).
@@ -141,7 +145,7 @@ int phikron_apply_many(phikron_plan_t plan, int nrhs, const double* V, double* O
 int phikron_apply_host(phikron_plan_t plan, const double* V_host, double* Out_host, void* stream);
 
 typedef struct phikron_info {
-  int    dims, n[3];
+  int    dims, n[PHIKRON_MAX_DIMS];
   int64_t N;
   int    l_max;
   int    s;            /* scaling exponent (paper's l)                                  */

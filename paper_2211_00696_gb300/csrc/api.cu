@@ -119,6 +119,7 @@ bool is_symmetric(const double* a, int n) {
 int select_mlp(int dims, const double* const* A, const int* n, double tau, int l_max, double tol, int* s, int* m) {
   std::vector<float> params;
   if (!mlp::model(&params)) return -1;
+  if (dims > 3) return 3;  // the network's features describe at most three factors
   double tn[3] = {0, 0, 0}, glo = 0.0, ghi = 0.0;
   bool sym = true;
   for (int d = 0; d < dims; ++d) {
@@ -182,7 +183,7 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
     P.n[d] = n[d];
     P.N *= n[d];
   }
-  for (int d = dims; d < 3; ++d) P.n[d] = 1;
+  for (int d = dims; d < PHIKRON_MAX_DIMS; ++d) P.n[d] = 1;
 
   // alpha = tau * sum_d ||A^d||_inf  (Eq. (31))
   double alpha = 0.0;
@@ -423,7 +424,7 @@ int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const in
   clear_error();
   if (!out) { set_error("phikron_plan: out is NULL"); return PHIKRON_EINVAL; }
   *out = nullptr;
-  if (dims != 2 && dims != 3) { set_error("phikron_plan: dims must be 2 or 3"); return PHIKRON_EINVAL; }
+  if (dims < 1 || dims > PHIKRON_MAX_DIMS) { set_error("phikron_plan: dims must be in 1..PHIKRON_MAX_DIMS"); return PHIKRON_EINVAL; }
   if (!A || !n) { set_error("phikron_plan: A or n is NULL"); return PHIKRON_EINVAL; }
   if (!std::isfinite(tau)) { set_error("phikron_plan: tau must be finite"); return PHIKRON_EINVAL; }
   if (l_max < 0 || l_max > 20) { set_error("phikron_plan: l_max must be in 0..20"); return PHIKRON_EINVAL; }
@@ -518,7 +519,7 @@ int phikron_plan_info(phikron_plan_t plan, phikron_info* info) {
   const Plan& P = plan->impl;
   std::memset(info, 0, sizeof(*info));
   info->dims = P.dims;
-  for (int d = 0; d < 3; ++d) info->n[d] = P.n[d];
+  for (int d = 0; d < PHIKRON_MAX_DIMS; ++d) info->n[d] = P.n[d];
   info->N = P.N;
   info->l_max = P.p;
   info->s = P.s;
@@ -627,7 +628,7 @@ int phikron_setup_quadrature(double eps, int p, double alpha, double beta, int r
 int phikron_selector_features(int dims, const int* n, const double* tau_norm_inf, int l_max, double tol,
                               float* out8) {
   clear_error();
-  if ((dims != 2 && dims != 3) || !n || !tau_norm_inf || !out8 || l_max < 0 || !(tol > 0.0)) {
+  if (dims < 1 || dims > 3 || !n || !tau_norm_inf || !out8 || l_max < 0 || !(tol > 0.0)) {
     set_error("phikron_selector_features: bad arguments");
     return PHIKRON_EINVAL;
   }
@@ -656,7 +657,7 @@ int phikron_expm_batched(int count, int n, const double* A, const double* scale,
 int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const double* V,
                            double* Out, double* work, void* stream) {
   clear_error();
-  if ((dims != 2 && dims != 3) || !n || !E || !V || !Out || !work) {
+  if (dims < 1 || dims > PHIKRON_MAX_DIMS || !n || !E || !V || !Out || !work) {
     set_error("phikron_kron_apply_f64: bad arguments");
     return PHIKRON_EINVAL;
   }

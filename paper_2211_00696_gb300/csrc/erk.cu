@@ -35,8 +35,8 @@ struct Csr {
 };
 
 struct KronCsr {
-  Csr f[3];
-  int n[3];
+  Csr f[PHIKRON_MAX_DIMS];
+  int n[PHIKRON_MAX_DIMS];
   int dims;
 };
 
@@ -98,7 +98,7 @@ using namespace phikron;
 
 struct phikron_erk_s {
   int method = 0, dims = 0, nonlin = 0;
-  int n[3] = {1, 1, 1};
+  int n[PHIKRON_MAX_DIMS] = {1, 1, 1, 1, 1, 1};
   long long N = 0;
   double tau = 0.0;
   int device = -1;
@@ -205,7 +205,10 @@ int phikron_erk_create(phikron_erk_t* out, int method, int dims, const double* c
     return PHIKRON_EINVAL;
   }
   if (!(tau > 0.0) || !std::isfinite(tau)) { set_error("phikron_erk_create: tau must be > 0"); return PHIKRON_EINVAL; }
-  if ((dims != 2 && dims != 3) || !A || !n) { set_error("phikron_erk_create: dims must be 2 or 3"); return PHIKRON_EINVAL; }
+  if (dims < 1 || dims > PHIKRON_MAX_DIMS || !A || !n) {
+    set_error("phikron_erk_create: dims must be in 1..PHIKRON_MAX_DIMS");
+    return PHIKRON_EINVAL;
+  }
   phikron_opts o;
   phikron_opts_default(&o);
   if (opts) o = *opts;

@@ -333,10 +333,10 @@ void slice_matrix_host(const double* E, int n, int slices, uint8_t* out, int* re
 struct MixedState {
   int slices = 5;
   int nsm = 148;
-  uint8_t* dSl[3] = {nullptr, nullptr, nullptr};  // per unique factor: nexp sliced matrices
-  int* dRexp[3] = {nullptr, nullptr, nullptr};     // per unique factor: nexp x nhalves x 128
-  size_t mat_bytes[3] = {0, 0, 0};
-  int rexp_stride[3] = {128, 128, 128};
+  uint8_t* dSl[PHIKRON_MAX_DIMS] = {};             // per unique factor: nexp sliced matrices
+  int* dRexp[PHIKRON_MAX_DIMS] = {};                // per unique factor: nexp x row blocks x 128
+  size_t mat_bytes[PHIKRON_MAX_DIMS] = {};
+  int rexp_stride[PHIKRON_MAX_DIMS] = {};
   float2* dCoefFF = nullptr;
   Seq seq;                                         // launch sequence of a single-vector apply
 };

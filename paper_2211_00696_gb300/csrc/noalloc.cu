@@ -61,7 +61,7 @@ extern "C" long long phikron_noalloc_max_elements(void) { return kMaxElems; }
 extern "C" int phikron_kron_apply_f64_noalloc(int dims, const int* n, const double* const* E, const double* V,
                                               double* Out, void* stream) {
   clear_error();
-  if ((dims != 2 && dims != 3) || !n || !E || !V || !Out) {
+  if (dims < 1 || dims > PHIKRON_MAX_DIMS || !n || !E || !V || !Out) {
     set_error("phikron_kron_apply_f64_noalloc: bad arguments");
     return PHIKRON_EINVAL;
   }

@@ -10,7 +10,7 @@ namespace phikron {
 
 struct Plan {
   int dims = 0;
-  int n[3] = {1, 1, 1};
+  int n[PHIKRON_MAX_DIMS] = {1, 1, 1, 1, 1, 1};
   long long N = 0;
   double tau = 0.0;
   int p = 0;            // l_max: orders 0..p are returned
@@ -23,14 +23,14 @@ struct Plan {
 
   // unique factors: uniq_of[d] -> u, uniq_rep[u] -> first d
   int nuniq = 0;
-  int uniq_of[3] = {0, 0, 0};
-  int uniq_rep[3] = {0, 0, 0};
+  int uniq_of[PHIKRON_MAX_DIMS] = {0, 0, 0, 0, 0, 0};
+  int uniq_rep[PHIKRON_MAX_DIMS] = {0, 0, 0, 0, 0, 0};
   // per unique factor, nexp = m + 1 + s float64 matrices n_d x n_d:
   //   [0, m)       E_k = exp((1 - x_k) 2^{-s} M^d)
   //   m            exp(M^d)                      (phi_0)
   //   m + 1 + t    G_t = exp(2^{t-s} M^d), t < s (squaring steps)
   int nexp = 0;
-  double* dExp[3] = {nullptr, nullptr, nullptr};
+  double* dExp[PHIKRON_MAX_DIMS] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* dCoef = nullptr;
 
   // float64 apply work buffers

@@ -39,7 +39,7 @@ class Opts(C.Structure):
 
 
 class Info(C.Structure):
-    _fields_ = [("dims", C.c_int), ("n", C.c_int * 3), ("N", C.c_int64), ("l_max", C.c_int),
+    _fields_ = [("dims", C.c_int), ("n", C.c_int * 6), ("N", C.c_int64), ("l_max", C.c_int),
                 ("s", C.c_int), ("m", C.c_int), ("cost", C.c_int), ("actions", C.c_int),
                 ("alpha", C.c_double), ("log10_bound", C.c_double), ("precision", C.c_int),
                 ("quad", C.c_int), ("selector_used", C.c_int), ("unique_factors", C.c_int),
