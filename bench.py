@@ -334,7 +334,8 @@ def run_ours(args):
     prob = workload()
     v = prob.vector()
     t0 = time.perf_counter()
-    plan = pk.Plan(prob.factors, prob.tau, prob.l_max, tol, precision=prec_id, device=local)
+    quad = {"gauss": pk.QUAD_GAUSS, "cc": pk.QUAD_CC, "cc_adaptive": pk.QUAD_CC_ADAPTIVE}[args.quad]
+    plan = pk.Plan(prob.factors, prob.tau, prob.l_max, tol, precision=prec_id, device=local, quad=quad)
     torch.cuda.synchronize()
     plan_ms = (time.perf_counter() - t0) * 1e3
     info = plan.info()
@@ -347,6 +348,7 @@ def run_ours(args):
     # accuracy on this run's output (sampled against stored oracle values)
     plan.apply(V, Out)
     torch.cuda.synchronize()
+    info = plan.info()               # adaptive quadrature: node count of this input
     golden = load_golden()
     errs = sampled_rel_err(Out.cpu().numpy(), golden) if golden is not None else None
 
@@ -421,7 +423,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": prob.name, "N": prob.N, "l_max": prob.l_max, "tau": prob.tau,
-                       "tol": tol, "precision": args.precision, "s": info["s"], "m": info["m"],
+                       "tol": tol, "precision": args.precision, "quad": args.quad, "s": info["s"],
+                       "m": info["adaptive_nodes"] if args.quad == "cc_adaptive" else info["m"],
                        "actions": info["actions"], "parallelism": f"replicas{world}",
                        "l2": "flushed (512 MiB write) before every timed step"},
             "rel_err_sampled": errs,
@@ -461,6 +464,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=list(PRECISIONS))
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    ap.add_argument("--quad", default="gauss", choices=["gauss", "cc", "cc_adaptive"],
+                    help="quadrature of the timed plan (cc_adaptive: Algorithm 2, float64 path only)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", default="convdiff3d", choices=["convdiff3d", "batched", "allen_cahn"])
     args = ap.parse_args()

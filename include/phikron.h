@@ -48,6 +48,15 @@ extern "C" {
 /* ------------------------------------------------------------------ options */
 #define PHIKRON_QUAD_GAUSS        0   /* Gauss-Legendre, Algorithm 1 (Sec. 3.1)            */
 #define PHIKRON_QUAD_CC           1   /* Clenshaw-Curtis nodes with the CC bound            */
+#define PHIKRON_QUAD_CC_ADAPTIVE  2   /* Algorithm 2: nested Clenshaw-Curtis rules with 7, 13,
+                                         25, ... nodes, doubled until the max-norm change of
+                                         every y_j is <= tol relative (s from Algorithm 5 with
+                                         the CC bound).  float64 path only; the apply reads an
+                                         error estimate back per refinement (synchronous).
+                                         Node cap: the first rule with >= 2x the a-priori CC
+                                         node count (>= 13 nodes, <= 385; opts.force_m raises
+                                         it); not converged at the cap -> ENOTCONVERGED with
+                                         the cap's result in Out.                             */
 
 #define PHIKRON_PREC_FP64         0   /* every product in float64 (DFMA)                    */
 #define PHIKRON_PREC_OZAKI_BF16   2   /* mixed: mode products on the tensor cores as exact
@@ -151,7 +160,7 @@ typedef struct phikron_info {
   int    s;            /* scaling exponent (paper's l)                                  */
   int    m;            /* number of quadrature nodes (paper's n+1)                      */
   int    cost;         /* m + s*l_max, Algorithm 5's C with c1 = 0, c2 = 1              */
-  int    actions;      /* Kronecker actions per apply: m + s*l_max + 1 (phi_0)          */
+  int    actions;      /* Kronecker actions per apply: m + s*l_max + 1 (phi_0); adaptive: nodes of the last apply */
   double alpha;        /* ||tau*A||_inf estimate used                                   */
   double log10_bound;  /* log10 of Algorithm 3's bound at the chosen (s, m)             */
   int    precision, quad;
@@ -159,6 +168,8 @@ typedef struct phikron_info {
   int    unique_factors;
   size_t device_bytes; /* device memory held by the plan                                */
   int    slices;       /* digit slices of the mixed path (0 for FP64)                   */
+  int    adaptive_nodes;  /* PHIKRON_QUAD_CC_ADAPTIVE: nodes used by the last apply (0 before)  */
+  double adaptive_err;    /* and its final error estimate (Algorithm 2's err)                  */
 } phikron_info;
 
 int  phikron_plan_info(phikron_plan_t plan, phikron_info* info);

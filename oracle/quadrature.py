@@ -1,5 +1,5 @@
-"""Algorithms 1 and 6 (fixed quadrature with scaling and modified squaring), restated
-step by step in float64 with library matrix exponentials.  Test infrastructure only.
+"""Algorithms 1, 2 and 6 (fixed and adaptive quadrature with scaling and modified squaring),
+restated step by step in float64 with library matrix exponentials.  Test infrastructure only.
 
 These follow the paper's order and notation and serve two purposes: (i) pin the
 reading of the paper against the plain definition (``phi.phi_dense``), and (ii) give
@@ -41,6 +41,51 @@ def alg1_fixed(Ms, v: np.ndarray, p: int, x: np.ndarray, w: np.ndarray):
     return ys
 
 
+def alg2_adaptive_cc(Ms, v: np.ndarray, p: int, tol: float, max_nodes: int = 385):
+    """Algorithm 2 for M = (+)_d Ms[d]: nested Clenshaw-Curtis rules with 2n+1 points, n = 3,
+    6, 12, ...; each refinement evaluates the integrand only at the new (odd-indexed) nodes and
+    re-forms y_j with the new rule's weights, until err = max_j ||y_j - y~_j||_inf / ||y_j||_inf
+    <= tol.  Returns (y_1..y_p, nodes used, final err).  Reading: a y_j that is zero with a
+    zero change counts as converged; a rule above max_nodes stops with err > tol."""
+    shape = tuple(a.shape[0] for a in Ms)
+    V = np.asarray(v, dtype=np.float64).reshape(shape)
+
+    def integrand(xi):
+        return apply_kron([scipy.linalg.expm((1.0 - xi) * a) for a in Ms], V).ravel()
+
+    def weighted(x, w, vs):
+        ys = []
+        for j in range(1, p + 1):
+            y = np.zeros(V.size)
+            for i in range(len(x)):
+                y += w[i] * x[i] ** (j - 1) / math.factorial(j - 1) * vs[i]
+            ys.append(y)
+        return ys
+
+    n = 3
+    x, w = planner.clenshaw_curtis_01(2 * n)
+    vs = [integrand(xi) for xi in x]
+    y = weighted(x, w, vs)
+    err = math.inf
+    while err > tol:
+        if 4 * n + 1 > max_nodes:
+            break
+        n = 2 * n
+        ytil = y
+        x, w = planner.clenshaw_curtis_01(2 * n)
+        new = [None] * (2 * n + 1)
+        for i in range(2 * n + 1):
+            new[i] = vs[i // 2] if i % 2 == 0 else integrand(x[i])   # even points are the old rule's
+        vs = new
+        y = weighted(x, w, vs)
+        err = 0.0
+        for j in range(p):
+            d = np.max(np.abs(y[j] - ytil[j]))
+            m_ = np.max(np.abs(y[j]))
+            err = max(err, d / m_ if m_ > 0 else (math.inf if d > 0 else 0.0))
+    return y, len(x), err
+
+
 def alg6_phiquadmv(factors, tau: float, v: np.ndarray, p: int, tol: float,
                    s: int | None = None, m: int | None = None, rule: str = planner.GAUSS,
                    return_stages: bool = False):
@@ -58,15 +103,19 @@ def alg6_phiquadmv(factors, tau: float, v: np.ndarray, p: int, tol: float,
         return (out, stages) if return_stages else out
     if s is None or m is None:
         alpha = planner.alpha_inf(factors, tau)
-        s_, m_, _ = planner.setup_quadrature(tol, p, alpha, 1.0, rule)
+        s_, m_, _ = planner.setup_quadrature(tol, p, alpha, 1.0, planner.CC if rule == "cc_adaptive" else rule)
         s = s_ if s is None else s
         m = m_ if m is None else m
-    if rule == planner.GAUSS:
-        x, w = planner.gauss_legendre_01(m)
-    else:
-        x, w = planner.clenshaw_curtis_01(m - 1)
     scaled = [a / 2.0 ** s for a in Ms]
-    y = alg1_fixed(scaled, V.ravel(), p, x, w)
+    if rule == "cc_adaptive":
+        y, used, err = alg2_adaptive_cc(scaled, V.ravel(), p, tol)
+        stages["nodes"], stages["err"] = used, err
+    else:
+        if rule == planner.GAUSS:
+            x, w = planner.gauss_legendre_01(m)
+        else:
+            x, w = planner.clenshaw_curtis_01(m - 1)
+        y = alg1_fixed(scaled, V.ravel(), p, x, w)
     stages["scaled"] = [yy.copy() for yy in y]
     F = [scipy.linalg.expm(a) for a in scaled]          # e^{2^{-s} M^d}
     for k in range(s):

@@ -5,5 +5,5 @@ its Python binding (``phikron``) and build script (``build``).
 """
 from .phikron import (Plan, Batch, Integrator, PhikronError, lib, log_quaderr, quadnodes, setup_quadrature,  # noqa: F401
                       gauss_legendre, clenshaw_curtis, expm_batched, kron_apply_f64,
-                      PREC_FP64, PREC_OZAKI_BF16, QUAD_GAUSS, QUAD_CC,
+                      PREC_FP64, PREC_OZAKI_BF16, QUAD_GAUSS, QUAD_CC, QUAD_CC_ADAPTIVE,
                       ERK_EULER, ERK_RK2, ERK_RK3, NONLIN_NONE, NONLIN_ALLEN_CAHN)

@@ -197,7 +197,10 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
   const double beta = (o.beta > 0.0) ? o.beta : 1.0;
   P.log10_bound = -INFINITY;
 
-  // (s, m): Algorithm 5, unless forced or trivial
+  // (s, m): Algorithm 5, unless forced or trivial.  Adaptive Clenshaw-Curtis (Algorithm 2)
+  // takes s from Algorithm 5 with the CC bound and refines the node count at apply time.
+  const bool adaptive = (o.quad == PHIKRON_QUAD_CC_ADAPTIVE);
+  const int rule = adaptive ? PHIKRON_QUAD_CC : o.quad;
   int s = 0, m = 0, cost = 0;
   P.selector_used = PHIKRON_SELECT_PAPER;
   if (l_max >= 1) {
@@ -214,23 +217,36 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
     if (sel == 1 || sel == 2) {
       // (s, m) from the network, checked
     } else if (alpha > 0.0) {
-      PK_RET(planner::setup_quadrature(tol, l_max, alpha, beta, o.quad, &s, &m, &cost));
+      PK_RET(planner::setup_quadrature(tol, l_max, alpha, beta, rule, &s, &m, &cost));
     } else {
       s = 0;
       m = (l_max + 1) / 2 + 1;  // M = 0: the integrand is a polynomial of degree l_max-1
     }
     if (o.force_s >= 0) s = o.force_s;
-    if (o.force_m >= 1) m = o.force_m;
+    if (adaptive) {
+      // levels l = 0..L with 6*2^l + 1 nodes (Algorithm 2 starts at n = 3: 2n + 1 = 7); the
+      // cap is the first rule with at least twice the a-priori CC node count (force_m: at
+      // least force_m nodes), never below one refinement and never above 385 nodes
+      const int want = (o.force_m >= 1) ? o.force_m : 2 * m;
+      int L = 1;
+      while (L < 6 && 6 * (1 << L) + 1 < want) ++L;
+      P.ad_levels = L;
+      P.ad_nodes.clear();
+      for (int l = 0; l <= L; ++l) P.ad_nodes.push_back(6 * (1 << l) + 1);
+      m = P.ad_nodes.back();
+    } else if (o.force_m >= 1) {
+      m = o.force_m;
+    }
     if (o.half_step && s < 1) s = 1;  // the half-step state is the one before the last squaring
     if (o.quad == PHIKRON_QUAD_CC && m < 2) m = 2;
-    if (m > 256 || s > 60) {
+    if ((m > 256 && !adaptive) || s > 60) {
       set_error("plan: node count or scaling out of range (m <= 256, s <= 60)");
       return PHIKRON_EINVAL;
     }
     if (alpha > 0.0) {
       double lb;
       if (planner::log_quaderr(std::max(1.0, (double)(m - 1)), l_max, std::ldexp(alpha, -s), beta,
-                               o.quad, &lb) == PHIKRON_OK)
+                               rule, &lb) == PHIKRON_OK)
         P.log10_bound = lb / std::log(10.0);
       clear_error();
     }
@@ -242,17 +258,54 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
   // quadrature rule and node weights c_{j,k} = w_k x_k^{j-1}/(j-1)!  (Algorithm 1)
   P.x.assign(m, 0.0);
   P.w.assign(m, 0.0);
-  if (m > 0) {
-    if (o.quad == PHIKRON_QUAD_GAUSS)
-      PK_RET(planner::gauss_legendre(m, P.x.data(), P.w.data()));
-    else
-      PK_RET(planner::clenshaw_curtis(m - 1, P.x.data(), P.w.data()));
-  }
-  P.coef.assign((size_t)std::max(1, l_max) * std::max(1, m), 0.0);
-  for (int j = 1; j <= l_max; ++j) {
-    double fact = 1.0;
-    for (int q = 2; q <= j - 1; ++q) fact *= q;
-    for (int k = 0; k < m; ++k) P.coef[(size_t)(j - 1) * m + k] = P.w[k] * std::pow(P.x[k], j - 1) / fact;
+  if (adaptive && l_max >= 1) {
+    // nodes of the finest rule (n_f = 6*2^L intervals) in order of first appearance: level l
+    // contributes the points j with j multiple of 2^{L-l} but not of 2^{L-l+1}
+    const int L = P.ad_levels, nf = 6 << L;
+    std::vector<double> xf(nf + 1), wf(nf + 1);
+    PK_RET(planner::clenshaw_curtis(nf, xf.data(), wf.data()));
+    std::vector<int> order;        // finest index of each stored node
+    for (int l = 0; l <= L; ++l) {
+      const int step = 1 << (L - l);
+      for (int j = 0; j <= nf; j += step)
+        if (l == 0 || (j / step) % 2 == 1) order.push_back(j);
+    }
+    for (int k = 0; k < m; ++k) {
+      P.x[k] = xf[order[k]];
+      P.w[k] = wf[order[k]];
+    }
+    // weights of every level's rule over its stored nodes: c_{j,k} = w_k^{(l)} x_k^{j-1}/(j-1)!
+    P.coef.clear();
+    P.ad_coef_off.clear();
+    for (int l = 0; l <= L; ++l) {
+      const int nl = 6 << l, cnt = P.ad_nodes[l], step = 1 << (L - l);
+      std::vector<double> xl(nl + 1), wl(nl + 1);
+      PK_RET(planner::clenshaw_curtis(nl, xl.data(), wl.data()));
+      P.ad_coef_off.push_back(P.coef.size());
+      const size_t base = P.coef.size();
+      P.coef.resize(base + (size_t)l_max * cnt);
+      for (int j = 1; j <= l_max; ++j) {
+        double fact = 1.0;
+        for (int q = 2; q <= j - 1; ++q) fact *= q;
+        for (int k = 0; k < cnt; ++k) {
+          const int jl = order[k] / step;  // index of stored node k in the level-l rule
+          P.coef[base + (size_t)(j - 1) * cnt + k] = wl[jl] * std::pow(xl[jl], j - 1) / fact;
+        }
+      }
+    }
+  } else {
+    if (m > 0) {
+      if (o.quad == PHIKRON_QUAD_GAUSS)
+        PK_RET(planner::gauss_legendre(m, P.x.data(), P.w.data()));
+      else
+        PK_RET(planner::clenshaw_curtis(m - 1, P.x.data(), P.w.data()));
+    }
+    P.coef.assign((size_t)std::max(1, l_max) * std::max(1, m), 0.0);
+    for (int j = 1; j <= l_max; ++j) {
+      double fact = 1.0;
+      for (int q = 2; q <= j - 1; ++q) fact *= q;
+      for (int k = 0; k < m; ++k) P.coef[(size_t)(j - 1) * m + k] = P.w[k] * std::pow(P.x[k], j - 1) / fact;
+    }
   }
 
   // unique factors (bitwise-equal matrices share their exponentials)
@@ -329,7 +382,14 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
 
   // apply work buffers
   const long long N = P.N;
-  const int nv = std::max(m + 2, std::max(l_max, 1));
+  int nv = std::max(m + 2, std::max(l_max, 1));
+  if (P.ad_levels >= 0) {
+    // node vectors kept across refinements; the mode chain of one level needs room for its
+    // new nodes only
+    nv = std::max(P.ad_nodes[P.ad_levels] - P.ad_nodes[P.ad_levels - 1] + 2, std::max(l_max, 1));
+    PK_RET(P.alloc((void**)&P.dT, sizeof(double) * (size_t)m * N));
+    PK_RET(P.alloc((void**)&P.dErr, sizeof(unsigned long long) * 2 * (size_t)l_max));
+  }
   PK_RET(P.alloc((void**)&P.dW1, sizeof(double) * (size_t)nv * N));
   PK_RET(P.alloc((void**)&P.dW2, sizeof(double) * (size_t)nv * N));
   PK_RET(P.alloc((void**)&P.dY, sizeof(double) * (size_t)std::max(l_max, 1) * N));
@@ -363,9 +423,93 @@ int kron_chain_f64(const Plan& P, const double* src, long long src_sb, int nvec,
   return PHIKRON_OK;
 }
 
+// Algorithm 2's error: max_j ||y_j - y~_j||_inf / ||y_j||_inf; slots[2j] and slots[2j+1] receive
+// the bit patterns of max|y_j - y~_j| and max|y_j| (non-negative doubles order like integers)
+__global__ void cc_err_kernel(const double* __restrict__ Y, const double* __restrict__ Yo, int p, long long N,
+                              unsigned long long* __restrict__ slots) {
+  for (int j = 0; j < p; ++j) {
+    double dmax = 0.0, ymax = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+      const double y = Y[(size_t)j * N + i];
+      dmax = fmax(dmax, fabs(y - Yo[(size_t)j * N + i]));
+      ymax = fmax(ymax, fabs(y));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(slots + 2 * j, (unsigned long long)__double_as_longlong(dmax));
+      atomicMax(slots + 2 * j + 1, (unsigned long long)__double_as_longlong(ymax));
+    }
+  }
+}
+
+// Algorithm 3 with Algorithm 2: nested Clenshaw-Curtis rules on 2^{-s}M, refined until the
+// max-norm change of every y_j is <= tol relative, then the s squaring steps.
+int apply_f64_adaptive(Plan& P, const double* V, double* Out, cudaStream_t st) {
+  const long long N = P.N;
+  const int p = P.p, m = P.m, s = P.s, L = P.ad_levels;
+  if (!P.opts.skip_phi0) PK_RET(kron_chain_f64(P, V, 0, 1, m, 0, P.dW1, P.dW2, Out, st));
+  double* bufs[2] = {P.dY, P.dYn};
+  int cur = 0, done = 0;
+  double err = INFINITY;
+  int used = 0;
+  for (int l = 0; l <= L; ++l) {
+    const int nl = P.ad_nodes[l];
+    // v_i = e^{(1 - x_i) 2^{-s} M} v for the nodes this rule adds (stored after the earlier ones)
+    PK_RET(kron_chain_f64(P, V, 0, nl - done, done, 1, P.dW1, P.dW2, P.dT + (size_t)done * N, st));
+    done = nl;
+    used = nl;
+    PK_RET(weighted_sum_f64(P.dT, N, P.dCoef + P.ad_coef_off[l], p, nl, N, bufs[cur], N, st));
+    if (l >= 1) {
+      PK_TRY_CUDA(cudaMemsetAsync(P.dErr, 0, sizeof(unsigned long long) * 2 * p, st));
+      cc_err_kernel<<<(int)std::min<long long>((N + 255) / 256, 152 * 4), 256, 0, st>>>(bufs[cur], bufs[cur ^ 1], p,
+                                                                                      N, P.dErr);
+      PK_CHECK_LAUNCH();
+      std::vector<unsigned long long> h(2 * p);
+      PK_TRY_CUDA(cudaMemcpyAsync(h.data(), P.dErr, sizeof(unsigned long long) * 2 * p, cudaMemcpyDeviceToHost, st));
+      PK_TRY_CUDA(cudaStreamSynchronize(st));
+      err = 0.0;
+      for (int j = 0; j < p; ++j) {
+        double dm, ym;
+        std::memcpy(&dm, &h[2 * j], sizeof(double));
+        std::memcpy(&ym, &h[2 * j + 1], sizeof(double));
+        // a zero y_j with a zero change counts as converged
+        err = std::max(err, (ym > 0.0) ? dm / ym : (dm > 0.0 ? INFINITY : 0.0));
+      }
+      if (err <= P.tol) break;
+    }
+    cur ^= 1;
+  }
+  if (!(err <= P.tol)) cur ^= 1;  // the loop left cur one past the last level's buffer
+  P.last_nodes = used;
+  P.last_err = err;
+  double* Y = bufs[cur];
+  double* Yn = bufs[cur ^ 1];
+  if (s == 0) {
+    PK_TRY_CUDA(cudaMemcpyAsync(Out + N, Y, sizeof(double) * (size_t)p * N, cudaMemcpyDeviceToDevice, st));
+  } else {
+    for (int t = 0; t < s; ++t) {
+      double* Z = (P.dims % 2 == 1) ? P.dW1 : P.dW2;
+      PK_RET(kron_chain_f64(P, Y, N, p, m + 1 + t, 0, P.dW1, P.dW2, Z, st));
+      double* dst = (t == s - 1) ? Out + N : Yn;
+      PK_RET(squaring_combine_f64(Z, Y, dst, p, N, N, st));
+      Yn = Y;
+      Y = dst;
+    }
+  }
+  if (!(err <= P.tol)) {
+    set_error("adaptive Clenshaw-Curtis: not converged at the node cap (Out holds the cap's result)");
+    return PHIKRON_ENOTCONVERGED;
+  }
+  return PHIKRON_OK;
+}
+
 int apply_f64(Plan& P, const double* V, double* Out, cudaStream_t st) {
   const long long N = P.N;
   const int p = P.p, m = P.m, s = P.s;
+  if (P.ad_levels >= 0 && p >= 1) return apply_f64_adaptive(P, V, Out, st);
   if (p == 0) {
     // phi_0 only: (x)_d exp(M^d) v
     return kron_chain_f64(P, V, 0, 1, m, 0, P.dW1, P.dW2, Out, st);
@@ -441,7 +585,14 @@ int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const in
   phikron_opts o;
   phikron_opts_default(&o);
   if (opts) o = *opts;
-  if (o.quad != PHIKRON_QUAD_GAUSS && o.quad != PHIKRON_QUAD_CC) { set_error("phikron_plan: bad quad"); return PHIKRON_EINVAL; }
+  if (o.quad != PHIKRON_QUAD_GAUSS && o.quad != PHIKRON_QUAD_CC && o.quad != PHIKRON_QUAD_CC_ADAPTIVE) {
+    set_error("phikron_plan: bad quad");
+    return PHIKRON_EINVAL;
+  }
+  if (o.quad == PHIKRON_QUAD_CC_ADAPTIVE && o.precision != PHIKRON_PREC_FP64) {
+    set_error("phikron_plan: adaptive Clenshaw-Curtis runs on the float64 path");
+    return PHIKRON_ENOTSUP;
+  }
   if (o.precision != PHIKRON_PREC_FP64 && o.precision != PHIKRON_PREC_OZAKI_BF16) { set_error("phikron_plan: bad precision"); return PHIKRON_EINVAL; }
   if (o.max_rhs < 1) o.max_rhs = 1;
   if (o.half_step && o.precision != PHIKRON_PREC_OZAKI_BF16) {
@@ -525,7 +676,8 @@ int phikron_plan_info(phikron_plan_t plan, phikron_info* info) {
   info->s = P.s;
   info->m = P.m;
   info->cost = P.cost;
-  info->actions = (P.p == 0) ? 1 : P.m + P.s * P.p + (P.opts.skip_phi0 ? 0 : 1);
+  const int nodes = (P.ad_levels >= 0 && P.last_nodes > 0) ? P.last_nodes : P.m;  // adaptive: last apply
+  info->actions = (P.p == 0) ? 1 : nodes + P.s * P.p + (P.opts.skip_phi0 ? 0 : 1);
   info->alpha = P.alpha;
   info->log10_bound = P.log10_bound;
   info->precision = P.opts.precision;
@@ -533,6 +685,8 @@ int phikron_plan_info(phikron_plan_t plan, phikron_info* info) {
   info->selector_used = P.selector_used;
   info->unique_factors = P.nuniq;
   info->device_bytes = P.device_bytes;
+  info->adaptive_nodes = P.last_nodes;
+  info->adaptive_err = P.last_err;
   info->slices = P.mixed ? mixed_slices(P) : 0;
   return PHIKRON_OK;
 }

@@ -33,6 +33,17 @@ struct Plan {
   double* dExp[PHIKRON_MAX_DIMS] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* dCoef = nullptr;
 
+  // adaptive Clenshaw-Curtis (Algorithm 2): levels 0..ad_levels with ad_nodes[l] = 6*2^l + 1
+  // nodes; nodes are stored in order of first appearance, so level l uses the first
+  // ad_nodes[l] exponentials; the weights of level l start at coef[ad_coef_off[l]] (p x nodes)
+  int ad_levels = -1;
+  std::vector<int> ad_nodes;
+  std::vector<size_t> ad_coef_off;
+  double* dT = nullptr;          // node vectors v_i, m x N
+  unsigned long long* dErr = nullptr;  // 2p reduction slots (bit patterns of non-negative doubles)
+  int last_nodes = 0;
+  double last_err = 0.0;
+
   // float64 apply work buffers
   double* dW1 = nullptr;
   double* dW2 = nullptr;

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libphikron.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONVERGED, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-QUAD_GAUSS, QUAD_CC = 0, 1
+QUAD_GAUSS, QUAD_CC, QUAD_CC_ADAPTIVE = 0, 1, 2
 PREC_FP64, PREC_OZAKI_BF16 = 0, 2
 SELECT_PAPER, SELECT_MLP = 0, 1
 SELECTOR_USED = {0: "algorithm5", 1: "network", 2: "network+m", 3: "fallback"}
@@ -43,7 +43,8 @@ class Info(C.Structure):
                 ("s", C.c_int), ("m", C.c_int), ("cost", C.c_int), ("actions", C.c_int),
                 ("alpha", C.c_double), ("log10_bound", C.c_double), ("precision", C.c_int),
                 ("quad", C.c_int), ("selector_used", C.c_int), ("unique_factors", C.c_int),
-                ("device_bytes", C.c_size_t), ("slices", C.c_int)]
+                ("device_bytes", C.c_size_t), ("slices", C.c_int), ("adaptive_nodes", C.c_int),
+                ("adaptive_err", C.c_double)]
 
 
 class Profile(C.Structure):

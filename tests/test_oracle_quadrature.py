@@ -40,3 +40,40 @@ def test_alg6_cc_rule_matches_O1():
     got = Q.alg6_phiquadmv(fac, tau, v, p, 1e-12, s=2, m=17, rule=PL.CC)
     for l in range(p + 1):
         assert P.rel_err_2(got[l], exact[l]) <= 1e-12
+
+
+# ----------------------------------------------------------------------------- Algorithm 2
+
+def test_clenshaw_curtis_rules_are_nested():
+    """Algorithm 2 reuses the integrand at the old nodes: the even points of the (2n+1)-point
+    rule are the (n+1)-point rule."""
+    from oracle import planner as PL
+    for n in (3, 6, 12, 24):
+        x2, _ = PL.clenshaw_curtis_01(2 * n)
+        x1, _ = PL.clenshaw_curtis_01(n)
+        assert np.array_equal(x2[::2], x1)
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10, 1e-13])
+def test_alg2_adaptive_matches_definition(tol):
+    fac = [W.convdiff_factor(5), W.laplacian_factor(4, 0.8), W.convdiff_factor(3)]
+    tau, p = 2e-2, 3
+    v = np.random.default_rng(4).uniform(-1, 1, 60)
+    out, st = Q.alg6_phiquadmv(fac, tau, v, p, tol, rule="cc_adaptive", return_stages=True)
+    exact = P.phi_dense(fac, tau, v, p)
+    assert st["err"] <= tol and st["nodes"] in (13, 25, 49, 97, 193, 385)
+    for l in range(p + 1):
+        assert P.rel_err_2(out[l], exact[l]) <= 5 * tol + 1e-14, (l, st)
+
+
+def test_alg2_diagonal_operator_gives_scalar_phi():
+    """Diagonal factors: y_j is phi_j of the diagonal entries (closed form via the scalar
+    recurrence), so the adaptive rule's result must meet its tolerance entrywise."""
+    d = [np.diag([-0.3, -2.0, -5.5]), np.diag([-0.1, -1.7])]
+    v = np.array([0.3, -1.0, 2.0, 0.5, -0.7, 1.1])
+    y, nodes, err = Q.alg2_adaptive_cc(d, v, 3, 1e-12)
+    z = (np.diag(d[0])[:, None] + np.diag(d[1])[None, :]).ravel()
+    for j in range(1, 4):
+        ref = P.phi_scalar(j, z) * v
+        assert np.max(np.abs(y[j - 1] - ref)) <= 1e-11 * np.max(np.abs(ref)), j
+    assert err <= 1e-12
