@@ -147,6 +147,18 @@ int phikron_apply(phikron_plan_t plan, const double* V, double* Out, void* strea
 int phikron_apply_many(phikron_plan_t plan, int nrhs, const double* V, double* Out, void* stream);
 
 /*
+ * phikron_apply_combo -- sum_{j=1}^{l_max} phi_j(-tau*A) b_j in one quadrature (the Remark
+ * after Algorithm 2): sum_i w_i e^{(1-x_i)M} sum_j x_i^{j-1}/(j-1)! b_j, M = -tau*A, i.e. m
+ * Kronecker actions instead of l_max * m.  The combination does not commute with the modified
+ * squaring, so the plan must have s = 0 (small tau*||A||, or opts.force_s = 0 with a node
+ * count that meets tol); otherwise EINVAL.  float64 path (a mixed plan returns ENOTSUP) with
+ * fixed rules (Gauss or CC).
+ *   B   : DEVICE, l_max*N float64 (b_j at B + (j-1)*N).
+ *   Out : DEVICE, N float64.  Asynchronous on stream.
+ */
+int phikron_apply_combo(phikron_plan_t plan, const double* B, double* Out, void* stream);
+
+/*
  * phikron_apply_host -- phikron_apply with HOST buffers: copies V (N float64) to the
  * plan's device staging buffer, applies, copies the (l_max+1)*N results back into Out.
  * Synchronous (returns when Out is filled).  Pinned host memory makes the copies faster.

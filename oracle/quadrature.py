@@ -86,6 +86,21 @@ def alg2_adaptive_cc(Ms, v: np.ndarray, p: int, tol: float, max_nodes: int = 385
     return y, len(x), err
 
 
+def remark_combo(factors, tau: float, B, x: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """The Remark after Algorithm 2: sum_j phi_j(M) b_j ~ sum_i w_i e^{(1-x_i)M} sum_j
+    x_i^{j-1}/(j-1)! b_j for M = -tau A (no scaling), B = [b_1, ..., b_p]."""
+    Ms = [-tau * np.asarray(a, dtype=np.float64) for a in factors]
+    shape = tuple(a.shape[0] for a in Ms)
+    out = np.zeros(int(np.prod(shape)))
+    for xi, wi in zip(x, w):
+        z = np.zeros_like(out)
+        for j in range(1, len(B) + 1):
+            z += xi ** (j - 1) / math.factorial(j - 1) * np.asarray(B[j - 1], dtype=np.float64)
+        mats = [scipy.linalg.expm((1.0 - xi) * a) for a in Ms]
+        out += wi * apply_kron(mats, z.reshape(shape)).ravel()
+    return out
+
+
 def alg6_phiquadmv(factors, tau: float, v: np.ndarray, p: int, tol: float,
                    s: int | None = None, m: int | None = None, rule: str = planner.GAUSS,
                    return_stages: bool = False):

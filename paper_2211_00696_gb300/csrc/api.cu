@@ -396,6 +396,21 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
   PK_RET(P.alloc((void**)&P.dYn, sizeof(double) * (size_t)std::max(l_max, 1) * N));
   PK_RET(P.alloc((void**)&P.dV, sizeof(double) * (size_t)N));
   PK_RET(P.alloc((void**)&P.dOut, sizeof(double) * (size_t)(l_max + 1) * (o.half_step ? 2 : 1) * N));
+  if (s == 0 && l_max >= 1 && m > 0 && o.precision == PHIKRON_PREC_FP64 && P.ad_levels < 0) {
+    // tables and buffer of phikron_apply_combo: [m x l_max] x_i^{j-1}/(j-1)!, then [m] w_i
+    std::vector<double> cb((size_t)m * l_max + m);
+    for (int i = 0; i < m; ++i) {
+      double t = 1.0;
+      for (int j = 1; j <= l_max; ++j) {
+        cb[(size_t)i * l_max + (j - 1)] = t;
+        t = t * P.x[i] / j;
+      }
+      cb[(size_t)m * l_max + i] = P.w[i];
+    }
+    PK_RET(P.alloc((void**)&P.dCombo, sizeof(double) * cb.size()));
+    PK_TRY_CUDA(cudaMemcpy(P.dCombo, cb.data(), sizeof(double) * cb.size(), cudaMemcpyHostToDevice));
+    PK_RET(P.alloc((void**)&P.dY2, sizeof(double) * (size_t)m * N));
+  }
   PK_RET(precision_setup(P));
   return PHIKRON_OK;
 }
@@ -504,6 +519,20 @@ int apply_f64_adaptive(Plan& P, const double* V, double* Out, cudaStream_t st) {
     return PHIKRON_ENOTCONVERGED;
   }
   return PHIKRON_OK;
+}
+
+// The Remark after Algorithm 2: sum_j phi_j(M) b_j ~ sum_i w_i e^{(1-x_i)M} z_i with
+// z_i = sum_j x_i^{j-1}/(j-1)! b_j (s = 0).  P.dCombo holds the m x p table x_i^{j-1}/(j-1)!
+// followed by the m weights w_i.
+int apply_combo_f64(Plan& P, const double* B, double* Out, cudaStream_t st) {
+  const long long N = P.N;
+  const int p = P.p, m = P.m;
+  double* Z = P.dY2;                                     // m vectors z_i
+  double* T = (P.dims % 2 == 1) ? P.dW1 : P.dW2;         // m vectors e^{(1-x_i)M} z_i
+  for (int c = 0; c < m; c += 20)  // the weighted-sum kernel forms at most 20 outputs per launch
+    PK_RET(weighted_sum_f64(B, N, P.dCombo + (size_t)c * p, std::min(20, m - c), p, N, Z + (size_t)c * N, N, st));
+  PK_RET(kron_chain_f64(P, Z, N, m, 0, 1, P.dW1, P.dW2, T, st));
+  return weighted_sum_f64(T, N, P.dCombo + (size_t)m * p, 1, m, N, Out, N, st);
 }
 
 int apply_f64(Plan& P, const double* V, double* Out, cudaStream_t st) {
@@ -644,6 +673,25 @@ int phikron_apply_many(phikron_plan_t plan, int nrhs, const double* V, double* O
   if (dg.rc != PHIKRON_OK) return dg.rc;
   ProfScope ps(&P.prof);
   return apply_dispatch(P, nrhs, V, Out, static_cast<cudaStream_t>(stream));
+}
+
+int phikron_apply_combo(phikron_plan_t plan, const double* B, double* Out, void* stream) {
+  clear_error();
+  if (!plan || !B || !Out) { set_error("phikron_apply_combo: NULL argument"); return PHIKRON_EINVAL; }
+  Plan& P = plan->impl;
+  if (P.opts.precision != PHIKRON_PREC_FP64 || P.ad_levels >= 0) {
+    set_error("phikron_apply_combo: runs on float64 plans with a fixed rule");
+    return PHIKRON_ENOTSUP;
+  }
+  if (P.s != 0 || P.p < 1 || !P.dCombo) {
+    set_error("phikron_apply_combo: needs a plan with s = 0 and l_max >= 1 (the combination does not "
+              "commute with the modified squaring)");
+    return PHIKRON_EINVAL;
+  }
+  DeviceGuard dg(P.opts.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  ProfScope ps(&P.prof);
+  return apply_combo_f64(P, B, Out, static_cast<cudaStream_t>(stream));
 }
 
 int phikron_apply_host(phikron_plan_t plan, const double* V_host, double* Out_host, void* stream) {

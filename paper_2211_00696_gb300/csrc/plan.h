@@ -44,6 +44,10 @@ struct Plan {
   int last_nodes = 0;
   double last_err = 0.0;
 
+  // the Remark's combination: [m x p] x_i^{j-1}/(j-1)!, then [m] w_i (allocated on first use)
+  double* dCombo = nullptr;
+  double* dY2 = nullptr;     // m vectors z_i
+
   // float64 apply work buffers
   double* dW1 = nullptr;
   double* dW2 = nullptr;
@@ -66,6 +70,7 @@ struct Plan {
 };
 
 int apply_f64(Plan& P, const double* V, double* Out, cudaStream_t st);
+int apply_combo_f64(Plan& P, const double* B, double* Out, cudaStream_t st);
 int apply_mixed(Plan& P, const double* V, double* Out, cudaStream_t st);
 // Reads and clears the device status word of the mixed path (synchronous).
 int mixed_status(Plan& P, int* status);

@@ -88,6 +88,7 @@ SIGNATURES = {
     "phikron_batch_get_info": (C.c_int, [C.c_void_p, C.POINTER(BatchInfo)]),
     "phikron_batch_check_status": (C.c_int, [C.c_void_p]),
     "phikron_batch_destroy": (None, [C.c_void_p]),
+    "phikron_apply_combo": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "phikron_erk_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(_DP), C.POINTER(C.c_int),
                                      C.c_double, C.c_double, C.c_int, C.POINTER(Opts)]),
     "phikron_erk_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -221,6 +222,14 @@ class Plan:
         self.l_max = l_max
         self.max_rhs = max_rhs
         self.nout = (l_max + 1) * (2 if half_step else 1)
+
+    def apply_combo(self, B, Out=None, stream=None):
+        """sum_j phi_j(-tau A) b_j for B of shape (l_max, N) (CUDA float64); plans with s = 0."""
+        import torch
+        if Out is None:
+            Out = torch.empty(self.N, dtype=torch.float64, device=B.device)
+        _check(lib().phikron_apply_combo(self._h, B.data_ptr(), Out.data_ptr(), _stream_ptr(stream)))
+        return Out
 
     def info(self) -> dict:
         inf = Info()

@@ -77,3 +77,17 @@ def test_alg2_diagonal_operator_gives_scalar_phi():
         ref = P.phi_scalar(j, z) * v
         assert np.max(np.abs(y[j - 1] - ref)) <= 1e-11 * np.max(np.abs(ref)), j
     assert err <= 1e-12
+
+
+def test_remark_combo_equals_sum_of_phi_actions():
+    """The Remark's single quadrature of sum_j phi_j(M) b_j agrees with the separate
+    phi-actions of the dense definition (Gauss rule, s = 0, small tau||A||)."""
+    from oracle import planner as PL
+    fac = [W.convdiff_factor(5), W.laplacian_factor(4, 0.5)]
+    tau, p = 4e-3, 3
+    rng = np.random.default_rng(6)
+    B = [rng.uniform(-1, 1, 20) for _ in range(p)]
+    x, w = PL.gauss_legendre_01(10)
+    got = Q.remark_combo(fac, tau, B, x, w)
+    ref = sum(P.phi_dense(fac, tau, B[j - 1], p)[j] for j in range(1, p + 1))
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
