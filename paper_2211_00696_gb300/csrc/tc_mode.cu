@@ -763,13 +763,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
         const uint32_t st = it & 1u, use = it >> 1;
         uint8_t* sX = smem + st * STAGE_BYTES;
         uint8_t* sE = sX + HALF_BYTES;
-        if (use >= 1 && !mbar_wait(smem_u32(&empty[st]), (use - 1) & 1u)) ws_fail(abort_s, status);
-        if (*abort_s) { stop = true; break; }
-        if (tid == 0) {
-          e_last = (int)it;
-          mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)HALF_BYTES);
-          bulk_copy_g2s(smem_u32(sE), S.ebase + (size_t)c * HALF_BYTES, (uint32_t)HALF_BYTES, smem_u32(&full_e[st]));
-        }
+        // the next chunk's raw values go in flight before the wait for a free stage, so that
+        // their latency overlaps the wait and this chunk's cutting
         Raw<IN_F64> rawn[2];
         if (c + 1 < nchunks) {
           ws_load<IN_F64, TRANS>(S, orow, 32 * (c + 1) + 16 * kh, rawn[0]);
@@ -781,6 +776,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
           } else {
             ws_fail(abort_s, status);
           }
+        }
+        if (use >= 1 && !mbar_wait(smem_u32(&empty[st]), (use - 1) & 1u)) ws_fail(abort_s, status);
+        if (*abort_s) { stop = true; break; }
+        if (tid == 0) {
+          e_last = (int)it;
+          mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)HALF_BYTES);
+          bulk_copy_g2s(smem_u32(sE), S.ebase + (size_t)c * HALF_BYTES, (uint32_t)HALF_BYTES, smem_u32(&full_e[st]));
         }
 #pragma unroll
         for (int g2 = 0; g2 < 2; ++g2) {
@@ -850,20 +852,27 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
           tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
           if (KS >= 4) tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
           tmem_wait_ld();
-          if (vg) {
+          // the float64 / float-float choice is made per group, so that the 16 columns of the
+          // unrolled body stay straight-line code the compiler can interleave
+          if (vg && !S.out_f64) {
+            float2* dst = reinterpret_cast<float2*>(S.out) + o0 + (long long)cc * S.R;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               float hi, lo;
               ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
               const float sc = scale_s[cc + j];
-              hi *= sc;
-              lo *= sc;
-              const long long oidx = o0 + (long long)(cc + j) * S.R;
-              if (S.out_f64)
-                reinterpret_cast<double*>(S.out)[oidx] = ff_to_f64(hi, lo);
-              else
-                reinterpret_cast<float2*>(S.out)[oidx] = make_float2(hi, lo);
-              mx = max(mx, __float_as_uint(hi) & 0x7FFFFFFFu);
+              dst[(long long)j * S.R] = make_float2(hi * sc, lo * sc);
+              mx = max(mx, __float_as_uint(hi * sc) & 0x7FFFFFFFu);
+            }
+          } else if (vg) {
+            double* dst = reinterpret_cast<double*>(S.out) + o0 + (long long)cc * S.R;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float hi, lo;
+              ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
+              const float sc = scale_s[cc + j];
+              dst[(long long)j * S.R] = ff_to_f64(hi * sc, lo * sc);
+              mx = max(mx, __float_as_uint(hi * sc) & 0x7FFFFFFFu);
             }
           }
         }
@@ -880,20 +889,28 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
           tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
           if (KS >= 4) tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
           tmem_wait_ld();
-          if (vi) {
+          const int jn = min(16, ncols - cc);  // columns of this group inside the tile
+          if (vi && !S.out_f64) {
+            float2* dst = reinterpret_cast<float2*>(S.out) + o0 + (long long)cc * S.n;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              if (cc + j >= ncols) break;
               float hi, lo;
               ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
-              hi *= sc;
-              lo *= sc;
-              const long long oidx = o0 + (long long)(cc + j) * S.n;
-              if (S.out_f64)
-                reinterpret_cast<double*>(S.out)[oidx] = ff_to_f64(hi, lo);
-              else
-                reinterpret_cast<float2*>(S.out)[oidx] = make_float2(hi, lo);
-              mx = max(mx, __float_as_uint(hi) & 0x7FFFFFFFu);
+              if (j < jn) {
+                dst[(long long)j * S.n] = make_float2(hi * sc, lo * sc);
+                mx = max(mx, __float_as_uint(hi * sc) & 0x7FFFFFFFu);
+              }
+            }
+          } else if (vi) {
+            double* dst = reinterpret_cast<double*>(S.out) + o0 + (long long)cc * S.n;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float hi, lo;
+              ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
+              if (j < jn) {
+                dst[(long long)j * S.n] = ff_to_f64(hi * sc, lo * sc);
+                mx = max(mx, __float_as_uint(hi * sc) & 0x7FFFFFFFu);
+              }
             }
           }
         }
