@@ -126,6 +126,26 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# DRAM traffic of the tensor-core mode kernel from the ncu capture summarised in
+# profiles/mode_kernel_ws_convdiff3d_n128_ncu_full.md (one launch of the z-mode node pass:
+# 9 vectors x N unknowns); valid only while the kernel source is the one captured.
+PROFILED_MODE_TRAFFIC = {"source_sha256_16": "24582c6a013f2f9d", "bytes": 152.646912e6 + 96.140288e6,
+                         "vector_passes": 9, "N": 2097152}
+
+
+def mode_traffic_per_launch(N, vector_passes_per_launch):
+    """dram read + write bytes per average mode launch, scaled from the capture by the number
+    of (vector, mode) products a launch processes; None if the kernel changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_2211_00696_gb300", "csrc", "tc_mode.cu")
+    with open(path, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    ref = PROFILED_MODE_TRAFFIC
+    if h != ref["source_sha256_16"] or N != ref["N"]:
+        return None
+    return ref["bytes"] * vector_passes_per_launch / ref["vector_passes"]
+
+
 def roofline(info, prof, ms_per_step_profiled, precision):
     """Roofline of the dominant kernel class from CUDA-event timings taken in bench.py."""
     pk, src = peaks()
@@ -152,15 +172,18 @@ def roofline(info, prof, ms_per_step_profiled, precision):
         gbs = prof["algorithmic_bytes"] / t / 1e9
         tfl = prof["bf16_flops"] / t / 1e12
         tpk = pk.get("bf16_tflops", 1900.0)
+        lps = launches / prof["steps"]
+        traffic = mode_traffic_per_launch(N, info["actions"] * info["dims"] / lps)
         if gbs / hbm >= tfl / tpk:
             return {"bound": "hbm", "kernel": "tc mode-product kernels (tcgen05 BF16 digit slices)",
                     "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                     "peak_source": f"{src} hbm_gbs", "tensor_frac": tfl / tpk,
-                    "avg_launch_ms": avg_ms, "launches_per_step": launches / prof["steps"], "traffic": None}
+                    "avg_launch_ms": avg_ms, "launches_per_step": lps, "traffic": traffic,
+                    "algorithmic_bytes_per_launch": prof["algorithmic_bytes"] / lps}
         return {"bound": "tensor", "kernel": "tc mode-product kernels (tcgen05 BF16 digit slices)",
                 "achieved": tfl, "peak": tpk, "unit": "TFLOP/s", "frac": tfl / tpk,
                 "peak_source": f"{src} bf16_tflops", "hbm_frac": gbs / hbm,
-                "avg_launch_ms": avg_ms, "launches_per_step": launches / prof["steps"], "traffic": None}
+                "avg_launch_ms": avg_ms, "launches_per_step": lps, "traffic": traffic}
     return {"bound": "hbm", "kernel": cls, "achieved": None, "peak": pk.get("hbm_gbs"),
             "unit": "GB/s", "frac": None, "traffic": None}
 
