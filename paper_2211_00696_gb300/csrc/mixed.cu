@@ -107,8 +107,8 @@ __device__ __forceinline__ void warp_max_atomic(int v, int* slot) {
 constexpr int MAXP = 8;
 constexpr int MAXM = 64;
 constexpr int EW_THREADS = 256;
-constexpr int EW_PER_THREAD = 4;
-constexpr long long EW_BLOCK = EW_THREADS * EW_PER_THREAD;
+constexpr int EW_PAIRS = 4;  // element pairs per thread (vectors are float2 arrays of even length)
+constexpr long long EW_BLOCK = 2LL * EW_THREADS * EW_PAIRS;
 
 struct InvFact {
   float2 f[MAXP + 1];  // 1/k! as float-float
@@ -127,6 +127,33 @@ __device__ __forceinline__ void* tab_ptr(const void* const* tab, int e, long lon
   return e >= 0 ? (void*)((char*)tab[e] + off) : direct;
 }
 
+// two consecutive float-float values (16 bytes; every vector offset used is a multiple of 2)
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+
+// stores of the results of one element pair: float-float (16-byte store) or float64 (two
+// 8-byte stores: the caller's float64 buffers need only be 8-byte aligned), plus the optional
+// float64 copy; the exponent maximum covers both
+__device__ __forceinline__ void st_pair(void* out, void* out2, bool f64, long long off, float2 a, float2 b, int& emax) {
+  if (f64) {
+    double* o = reinterpret_cast<double*>(out) + off;
+    o[0] = ff_to_f64(a.x, a.y);
+    o[1] = ff_to_f64(b.x, b.y);
+  } else {
+    *reinterpret_cast<float4*>(reinterpret_cast<float2*>(out) + off) = make_float4(a.x, a.y, b.x, b.y);
+  }
+  if (out2) {
+    double* o = reinterpret_cast<double*>(out2) + off;
+    o[0] = ff_to_f64(a.x, a.y);
+    o[1] = ff_to_f64(b.x, b.y);
+  }
+  emax = max(emax, (int)((__float_as_uint(a.x) >> 23) & 0xFFu));
+  emax = max(emax, (int)((__float_as_uint(b.x) >> 23) & 0xFFu));
+}
+
 // y_j = sum_k coef[j][k] T_k in float-float (Algorithm 1, second step), grouped over jobs
 template <int P_>
 __global__ void __launch_bounds__(EW_THREADS) g_weighted_kernel(const EJob* __restrict__ jobs, int njobs,
@@ -139,30 +166,31 @@ __global__ void __launch_bounds__(EW_THREADS) g_weighted_kernel(const EJob* __re
   __syncthreads();
   void* out = tab_ptr(ptrtab, J.out_tab, J.tab_off_out, J.out);
   void* out2 = tab_ptr(ptrtab, J.out2_tab, J.tab_off_out2, J.out2);
+  const bool f64 = J.out_f64 != 0;
+  const long long N = J.N, stride = J.stride;
   int emax[P_];
 #pragma unroll
   for (int j = 0; j < P_; ++j) emax[j] = 0;
   const long long base = (blockIdx.x - J.block_begin) * EW_BLOCK;
 #pragma unroll
-  for (int e = 0; e < EW_PER_THREAD; ++e) {
-    const long long i = base + e * EW_THREADS + threadIdx.x;
-    if (i >= J.N) break;
-    float2 acc[P_];
+  for (int e = 0; e < EW_PAIRS; ++e) {
+    const long long i = base + 2 * ((long long)e * EW_THREADS + threadIdx.x);
+    if (i < N) {
+      float2 acc0[P_], acc1[P_];
 #pragma unroll
-    for (int j = 0; j < P_; ++j) acc[j] = make_float2(0.f, 0.f);
-    for (int k = 0; k < m; ++k) {
-      const float2 t = J.a[k * J.stride + i];
+      for (int j = 0; j < P_; ++j) acc0[j] = acc1[j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int k = 0; k < m; ++k) {
+        float2 t0, t1;
+        ld_pair(J.a + k * stride + i, t0, t1);
 #pragma unroll
-      for (int j = 0; j < P_; ++j) ff_fma(acc[j], cs[j * m + k], t);
-    }
+        for (int j = 0; j < P_; ++j) {
+          ff_fma(acc0[j], cs[j * m + k], t0);
+          ff_fma(acc1[j], cs[j * m + k], t1);
+        }
+      }
 #pragma unroll
-    for (int j = 0; j < P_; ++j) {
-      if (J.out_f64)
-        reinterpret_cast<double*>(out)[j * J.stride + i] = ff_to_f64(acc[j].x, acc[j].y);
-      else
-        reinterpret_cast<float2*>(out)[j * J.stride + i] = acc[j];
-      if (out2) reinterpret_cast<double*>(out2)[j * J.stride + i] = ff_to_f64(acc[j].x, acc[j].y);
-      emax[j] = max(emax[j], (int)((__float_as_uint(acc[j].x) >> 23) & 0xFFu));
+      for (int j = 0; j < P_; ++j) st_pair(out, out2, f64, j * stride + i, acc0[j], acc1[j], emax[j]);
     }
   }
   if (J.out_exp) {
@@ -179,38 +207,43 @@ __global__ void __launch_bounds__(EW_THREADS) g_squaring_kernel(const EJob* __re
   const EJob& J = jobs[jb];
   void* out = tab_ptr(ptrtab, J.out_tab, J.tab_off_out, J.out);
   void* out2 = tab_ptr(ptrtab, J.out2_tab, J.tab_off_out2, J.out2);
+  const bool f64 = J.out_f64 != 0;
+  const long long N = J.N, stride = J.stride;
   int emax[P_];
 #pragma unroll
   for (int j = 0; j < P_; ++j) emax[j] = 0;
   const long long base = (blockIdx.x - J.block_begin) * EW_BLOCK;
 #pragma unroll
-  for (int e = 0; e < EW_PER_THREAD; ++e) {
-    const long long x = base + e * EW_THREADS + threadIdx.x;
-    if (x >= J.N) break;
-    float2 y[P_];
+  for (int e = 0; e < EW_PAIRS; ++e) {
+    const long long x = base + 2 * ((long long)e * EW_THREADS + threadIdx.x);
+    if (x < N) {
+      float2 y0[P_], y1[P_], z0[P_], z1[P_];
 #pragma unroll
-    for (int j = 0; j < P_; ++j) y[j] = J.b[j * J.stride + x];
-    float sc = 1.0f;
-#pragma unroll
-    for (int q = 1; q <= P_; ++q) {
-      sc *= 0.5f;
-      float2 acc = J.a[(q - 1) * J.stride + x];
-#pragma unroll
-      for (int j = 1; j <= q; ++j) {
-        const int d = q - j;
-        if (d <= 1)
-          ff_add(acc, y[j - 1]);
-        else
-          ff_fma(acc, inv.f[d], y[j - 1]);
+      for (int j = 0; j < P_; ++j) {
+        ld_pair(J.b + j * stride + x, y0[j], y1[j]);
+        ld_pair(J.a + j * stride + x, z0[j], z1[j]);
       }
-      acc.x *= sc;
-      acc.y *= sc;
-      if (J.out_f64)
-        reinterpret_cast<double*>(out)[(q - 1) * J.stride + x] = ff_to_f64(acc.x, acc.y);
-      else
-        reinterpret_cast<float2*>(out)[(q - 1) * J.stride + x] = acc;
-      if (out2) reinterpret_cast<double*>(out2)[(q - 1) * J.stride + x] = ff_to_f64(acc.x, acc.y);
-      emax[q - 1] = max(emax[q - 1], (int)((__float_as_uint(acc.x) >> 23) & 0xFFu));
+      float sc = 1.0f;
+#pragma unroll
+      for (int q = 1; q <= P_; ++q) {
+        sc *= 0.5f;
+        float2 a0 = z0[q - 1], a1 = z1[q - 1];
+#pragma unroll
+        for (int j = 1; j <= q; ++j) {
+          const int d = q - j;
+          if (d <= 1) {
+            ff_add(a0, y0[j - 1]);
+            ff_add(a1, y1[j - 1]);
+          } else {
+            ff_fma(a0, inv.f[d], y0[j - 1]);
+            ff_fma(a1, inv.f[d], y1[j - 1]);
+          }
+        }
+        z0[q - 1] = make_float2(a0.x * sc, a0.y * sc);
+        z1[q - 1] = make_float2(a1.x * sc, a1.y * sc);
+      }
+#pragma unroll
+      for (int q = 0; q < P_; ++q) st_pair(out, out2, f64, q * stride + x, z0[q], z1[q], emax[q]);
     }
   }
   if (J.out_exp) {
@@ -228,12 +261,13 @@ __global__ void __launch_bounds__(EW_THREADS) g_expscan_kernel(const EJob* __res
   int e = -1000;
   const long long base = (blockIdx.x - J.block_begin) * EW_BLOCK;
 #pragma unroll
-  for (int q = 0; q < EW_PER_THREAD; ++q) {
-    const long long i = base + q * EW_THREADS + threadIdx.x;
-    if (i >= J.N) break;
-    const uint64_t b = (uint64_t)__double_as_longlong(v[i]);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    if (ex != 0) e = max(e, ex - 1022);  // |x| < 2^{ex - 1023 + 1}
+  for (int q = 0; q < 2 * EW_PAIRS; ++q) {
+    const long long i = base + (long long)q * EW_THREADS + threadIdx.x;
+    if (i < J.N) {
+      const uint64_t b = (uint64_t)__double_as_longlong(__ldg(v + i));
+      const int ex = (int)((b >> 52) & 0x7FF);
+      if (ex != 0) e = max(e, ex - 1022);  // |x| < 2^{ex - 1023 + 1}
+    }
   }
   warp_max_atomic(e, J.out_exp);
 }
