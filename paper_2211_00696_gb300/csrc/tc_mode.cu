@@ -675,14 +675,23 @@ __device__ __forceinline__ void ws_load(const WsSlot& S, int orow, int kc, Raw<I
   }
 }
 
-// hi + lo ~ d2 + d3 + d4 + d5 (the level accumulators, largest first)
+// hi + lo ~ d2 + d3 + d4 + d5 (the level accumulators, largest first).  With at most 5 digit
+// slices the products are exact to ~2^-40 of the vector's scale, so only d2 + d3 needs an
+// error-free sum: d4 (~2^-16 of it) and d5 join the error term in plain FP32, which rounds at
+// ~2^-40.  Six slices (~2^-48) keep error-free sums at every step.
 template <int KS>
 __device__ __forceinline__ void ff_combine(float d2, float d3, float d4, float d5, float& hi, float& lo) {
-  float t45 = d4, e45 = 0.0f, u, eu, eh;
-  if (KS >= 4) two_sum(d4, d5, t45, e45);
-  two_sum(d3, t45, u, eu);
-  two_sum(d2, u, hi, eh);
-  lo = eh + (eu + e45);
+  if (KS <= 5) {
+    float eh;
+    two_sum(d2, d3, hi, eh);
+    lo = eh + (d4 + d5);
+  } else {
+    float t45, e45, u, eu, eh;
+    two_sum(d4, d5, t45, e45);
+    two_sum(d3, t45, u, eu);
+    two_sum(d2, u, hi, eh);
+    lo = eh + (eu + e45);
+  }
   fast_two_sum(hi, lo, hi, lo);
 }
 
