@@ -663,6 +663,21 @@ template <bool IN_F64, bool TRANS>
 __device__ __forceinline__ void ws_load(const WsSlot& S, int orow, int kc, Raw<IN_F64>& raw) {
   const long long gr = S.g0 + orow;
   const bool vr = TRANS ? (gr < S.R) : (gr < S.B0);
+  if (!TRANS && !IN_F64) {
+    // along a row of an internal float-float buffer: 16-byte loads (n is a multiple of 16 and
+    // every row starts 16-byte aligned), half the L1 wavefronts of 8-byte loads
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const int k = kc + e;
+      const bool ok = vr && k < S.n;
+      const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(S.in) +
+                                                                   gr * (long long)S.n + k))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      raw.f[e] = make_float2(v.x, v.y);
+      raw.f[e + 1] = make_float2(v.z, v.w);
+    }
+    return;
+  }
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int k = kc + e;
