@@ -346,8 +346,7 @@ void slice_matrix_host(const double* E, int n, int slices, uint8_t* out, int* re
       const uint64_t half = 1ull << (63 - 8 * slices);  // round to nearest at the last digit
       F = (F > ~0ull - half) ? ~0ull : F + half;
       const int c = k / KC, kk = k % KC;
-      const size_t off = (size_t)(i >> 3) * 512 + (size_t)(kk >> 3) * 128 + (size_t)(i & 7) * 16 +
-                         (size_t)(kk & 7) * 2;
+      const size_t off = (size_t)chunk_offset(i, kk >> 3) + (size_t)(kk & 7) * 2;
       for (int s = 0; s < slices; ++s) {
         const int t = s + 1;
         const uint32_t d = (uint32_t)((F >> (64 - 8 * t)) & 0xFFu);

@@ -40,6 +40,15 @@ struct PassShape {
   bool ws;                 // warp-specialised kernel (producer / MMA / epilogue warps)
 };
 
+// Shared-memory operand layout of one 128-row x 32-K BF16 slice (8 KiB), K-major, used by the
+// host slicing of E and by the kernels' digit cutting and MMA descriptors: the 64-byte swizzle
+// (8-row x 64-byte atoms of 512 B; the 16-byte chunk g of row r sits at chunk g ^ ((r >> 1) & 3)).
+constexpr bool kSwizzle64 = true;
+__host__ __device__ inline unsigned chunk_offset(int row, int g) {
+  return kSwizzle64 ? (unsigned)(row * 64 + ((g ^ ((row >> 1) & 3)) * 16))
+                    : (unsigned)((row >> 3) * 512 + g * 128 + (row & 7) * 16);
+}
+
 constexpr int MAX_PTRS = 128;
 struct PtrArgs {
   void* p[MAX_PTRS];

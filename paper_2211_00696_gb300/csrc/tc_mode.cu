@@ -62,14 +62,24 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 }
 
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
-  // no swizzle, K-major: LBO = 128 B (next core matrix along K), SBO = 512 B (next 8 rows)
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;
+  if (kSwizzle64) {
+    // 64-byte swizzle, K-major: SBO = 512 B (next 8-row atom); LBO unused (one atom spans K)
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)4 << 61;  // layout type: 64-byte swizzle
+  } else {
+    // no swizzle, K-major: LBO = 128 B (next core matrix along K), SBO = 512 B (next 8 rows)
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;
+  }
   d |= (uint64_t)1 << 46;  // descriptor version for sm_100-class tensor cores
   return d;
 }
+
+// byte offset of the 16-element K-step ks (0 or 1) inside a slice
+constexpr uint32_t KSTEP_BYTES = kSwizzle64 ? 32u : 256u;
 
 __device__ __forceinline__ uint32_t make_idesc(int M, int N) {
   // kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1), both K-major,
@@ -445,7 +455,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
             for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v0[sl], v1[sl]);
           }
         }
-        const uint32_t off = (uint32_t)(orow >> 3) * 512u + (uint32_t)kq * 128u + (uint32_t)(orow & 7) * 16u;
+        const uint32_t off = chunk_offset(orow, kq);
 #pragma unroll
         for (int sl = 0; sl < KS; ++sl)
           *reinterpret_cast<uint4*>(sX + (q * KS + sl) * SLICE_BYTES + off) =
@@ -470,8 +480,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
                 const uint32_t dacc = tmem + (uint32_t)(a * 128);
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
-                  const uint32_t xs = xa + (uint32_t)((q * KS + t - 1) * SLICE_BYTES + ks * 256);
-                  const uint32_t es = ea + (uint32_t)((q * KS + s - 1) * SLICE_BYTES + ks * 256);
+                  const uint32_t xs = xa + (uint32_t)((q * KS + t - 1) * SLICE_BYTES) + ks * KSTEP_BYTES;
+                  const uint32_t es = ea + (uint32_t)((q * KS + s - 1) * SLICE_BYTES) + ks * KSTEP_BYTES;
                   const uint64_t xd = make_desc(xs), ed = make_desc(es);
                   if (TRANS)
                     mma_bf16(dacc, xd, ed, idesc, init[a] ? 1u : 0u);
@@ -830,7 +840,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
             }
           }
           const int g = 2 * kh + g2;
-          const uint32_t off = (uint32_t)(orow >> 3) * 512u + (uint32_t)g * 128u + (uint32_t)(orow & 7) * 16u;
+          const uint32_t off = chunk_offset(orow, g);
 #pragma unroll
           for (int sl = 0; sl < KS; ++sl)
             *reinterpret_cast<uint4*>(sX + sl * SLICE_BYTES + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
@@ -978,8 +988,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
               const uint32_t dacc = tmem + (uint32_t)(a * 128);
 #pragma unroll
               for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t xd = make_desc(xa + (uint32_t)((t - 1) * SLICE_BYTES + ks * 256));
-                const uint64_t ed = make_desc(ea + (uint32_t)((s - 1) * SLICE_BYTES + ks * 256));
+                const uint64_t xd = make_desc(xa + (uint32_t)((t - 1) * SLICE_BYTES) + ks * KSTEP_BYTES);
+                const uint64_t ed = make_desc(ea + (uint32_t)((s - 1) * SLICE_BYTES) + ks * KSTEP_BYTES);
                 if (TRANS)
                   mma_bf16(dacc, xd, ed, idesc, init[a] ? 1u : 0u);
                 else
