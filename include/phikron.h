@@ -87,7 +87,7 @@ typedef struct phikron_opts {
   int    device;      /* CUDA device ordinal; -1 = the calling thread's current device        */
   int    max_rhs;     /* largest nrhs passed to phikron_apply_many; default 1                 */
   int    slices;      /* OZAKI_BF16: digit slices per operand, 3..6 (8 bits each; 3 ~ FP32,
-                         5 ~ 1e-12 per product); 0 = from tol (>=1e-5: 3, >=1e-7: 4,
+                         5 ~ 1e-12 per product); 0 = from tol (>=1e-5: 3, >=1e-8: 4,
                          >=1e-10: 5, else 6)                                                */
   int    half_step;   /* OZAKI_BF16 and l_max >= 1: also return phi_l(-tau/2*A) v, l = 0..l_max
                          (the state before the last squaring step of Eq. (29); s >= 1 is then
@@ -228,7 +228,7 @@ typedef struct phikron_batch_info {
   int       tuned;        /* 1 once the autotuner has run (or was not requested)             */
   double    best_ms;      /* time of the chosen shape during tuning (0 if not tuned)          */
   size_t    device_bytes; /* device memory held by the batch                                 */
-  int       ws_kernel;    /* 1 if the chosen mode kernel is the warp-specialised variant     */
+  int       ws_kernel;    /* chosen mode kernel: 2 double-buffered, 1 warp-specialised, 0 single-role */
 } phikron_batch_info;
 
 int  phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* plans, int nrhs,

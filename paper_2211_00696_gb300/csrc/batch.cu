@@ -148,10 +148,14 @@ int phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // candidate launch shapes
     std::vector<SeqConfig> cfgs;
-    const bool ws0 = mode_kernel_ws_default();
-    for (bool ws : {ws0, !ws0}) {
+    // kernel variants: 2 = double-buffered (where every n >= 64), 1 = warp-specialised,
+    // 0 = single-role; the default first, the others as autotuner candidates
+    const int v0 = mode_kernel_db_default() ? 2 : (mode_kernel_ws_default() ? 1 : 0);
+    std::vector<int> variants = {v0};
+    for (int v : {2, 1}) if (v != v0) variants.push_back(v);
+    for (int var : variants) {
       for (int sub : {1, 2}) {
-        if (sub == 2 && (slices != 3 || ws)) continue;  // 64-wide chunks: single-role kernel only
+        if (sub == 2 && (slices != 3 || var != 0)) continue;  // 64-wide chunks: single-role kernel only
         for (bool bf : {false, true}) {
           for (int g : {nsm, (3 * nsm) / 4}) {
             SeqConfig c;
@@ -161,7 +165,8 @@ int phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* 
             c.grid = g;
             c.big_first = bf;
             c.graph = true;
-            c.ws = ws;
+            c.ws = var >= 1;
+            c.db = var == 2;
             cfgs.push_back(c);
             if (!autotune) break;
           }
@@ -259,7 +264,7 @@ int phikron_batch_get_info(phikron_batch_t b, phikron_batch_info* info) {
   size_t bytes = b->work_bytes;
   for (const auto& s : b->cand) bytes += s->device_bytes;
   info->device_bytes = bytes;
-  info->ws_kernel = c.ws ? 1 : 0;
+  info->ws_kernel = c.db ? 2 : (c.ws ? 1 : 0);
   return PHIKRON_OK;
 }
 

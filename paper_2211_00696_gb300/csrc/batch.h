@@ -54,6 +54,7 @@ struct SeqConfig {
   bool big_first = false; // order the jobs of a pass by decreasing tile count
   bool graph = true;      // capture the sequence as a CUDA graph
   bool ws = true;         // warp-specialised mode kernel
+  bool db = false;        // double-buffered 128 x 64-tile mode kernel where every n >= 64
 };
 
 struct MixedView {
@@ -65,9 +66,11 @@ struct MixedView {
   int slices, nsm;
 };
 
-// Mode-kernel variant when nothing is tuned: the warp-specialised one, unless the environment
-// variable PHIKRON_MODE_KERNEL is "classic" (the single-role kernel).
+// Mode-kernel variant when nothing is tuned: the warp-specialised kernel, unless the environment
+// variable PHIKRON_MODE_KERNEL names another ("db": double-buffered 128 x 64 tiles where every
+// contracted size is at least 64; "classic": the single-role kernel).
 bool mode_kernel_ws_default();
+bool mode_kernel_db_default();
 
 const MixedView mixed_view(const Plan& P, int d);
 int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& cfg);

@@ -410,7 +410,9 @@ int precision_setup(Plan& P) {
   P.mixed = M;
   P.mixed_free = mixed_free;
   int slices = P.opts.slices;
-  if (slices <= 0) slices = (P.tol >= 1e-5) ? 3 : (P.tol >= 1e-7) ? 4 : (P.tol >= 1e-10) ? 5 : 6;
+  // digit error per apply measured on the 128^3 convection-diffusion workload: 3 slices ~4e-7,
+  // 4 ~2e-9, 5 ~1e-11, 6 below the float-float state's ~1e-13
+  if (slices <= 0) slices = (P.tol >= 1e-5) ? 3 : (P.tol >= 1e-8) ? 4 : (P.tol >= 1e-10) ? 5 : 6;
   if (slices < 3 || slices > 6) {
     set_error("mixed path: slices must be 3..6");
     return PHIKRON_EINVAL;
@@ -466,6 +468,7 @@ int precision_setup(Plan& P) {
   cfg.big_first = false;
   cfg.graph = true;
   cfg.ws = mode_kernel_ws_default();
+  cfg.db = mode_kernel_db_default();
   PK_RET(seq_build(M->seq, units, 1, cfg));
   return PHIKRON_OK;
 }
@@ -512,9 +515,9 @@ int seq_alloc(Seq& S, void** p, size_t bytes) {
   return PHIKRON_OK;
 }
 
-long long job_tiles(const GJob& j, bool trans) {
-  const long long halves = (j.n + 127) / 128;
-  return trans ? halves * j.B0 * ((j.R + 127) / 128) : halves * ((j.B0 + 127) / 128);
+long long job_tiles(const GJob& j, const PassShape& s) {
+  const long long blocks = (j.n + 127) / 128, f = tile_fibers(s);
+  return s.trans ? blocks * j.B0 * ((j.R + f - 1) / f) : blocks * ((j.B0 + f - 1) / f);
 }
 
 struct Builder {
@@ -528,12 +531,12 @@ struct Builder {
     if (jobs.empty()) return;
     if (big_first)
       std::stable_sort(jobs.begin(), jobs.end(), [&](const GJob& a, const GJob& b) {
-        return job_tiles(a, shape.trans) > job_tiles(b, shape.trans);
+        return job_tiles(a, shape) > job_tiles(b, shape);
       });
     long long t = 0;
     for (GJob& j : jobs) {
       j.tile_begin = t;
-      t += job_tiles(j, shape.trans);
+      t += job_tiles(j, shape);
     }
     Step s{};
     s.kind = STEP_MODE;
@@ -572,6 +575,11 @@ struct Builder {
 bool mode_kernel_ws_default() {
   const char* v = std::getenv("PHIKRON_MODE_KERNEL");
   return !(v && std::strcmp(v, "classic") == 0);
+}
+
+bool mode_kernel_db_default() {
+  const char* v = std::getenv("PHIKRON_MODE_KERNEL");
+  return v && std::strcmp(v, "db") == 0;
 }
 
 int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& cfg) {
@@ -717,6 +725,11 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       sh.in_f64 = (d == 0) && first_f64;
       sh.trans = trans;
       sh.ws = cfg.ws;
+      // the double-buffered kernel keeps two 32-wide chunks of a job in flight: n >= 64 in
+      // every job of the pass; smaller factors take the warp-specialised kernel
+      int minn = 1 << 30;
+      for (const GJob& j : jobs) minn = std::min(minn, j.n);
+      sh.db = cfg.db && minn >= 64;
       if (dims == 1) sh.trans = false;
       // all jobs of one pass share the formulation (same axis d)
       B.mode_step(jobs, sh);

@@ -38,6 +38,7 @@ struct PassShape {
   int grid;                // CTAs (persistent, 1 per SM at most)
   bool in_f64, trans;
   bool ws;                 // warp-specialised kernel (producer / MMA / epilogue warps)
+  bool db;                 // double-buffered 128 x 64 tiles (needs n >= 64 in every job)
 };
 
 // Shared-memory operand layout of one 128-row x 32-K BF16 slice (8 KiB), K-major, used by the
@@ -60,6 +61,9 @@ int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st);
 int set_ptrtab(void** tab, const PtrArgs& args, cudaStream_t st);
 size_t smem_bytes(int ks, int sub);
 }  // namespace tc
+
+// fibers per tile of a pass: 64 for the double-buffered kernel, 128 otherwise
+inline long long tile_fibers(const PassShape& s) { return s.db ? 64 : 128; }
 
 // Grouped float-float elementwise jobs (mixed.cu): weighted sums of Algorithm 1, modified
 // squaring of Eq. (29), and the exponent scan of a float64 input.

@@ -977,7 +977,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
             ws_fail(abort_s, status);
           if (*abort_s) { stop = true; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t xa = smem_u32(smem + st * STAGE_BYTES), ea = xa + HALF_BYTES;
+          // descriptors built once per chunk; the issue loop only adds compile-time offsets
+          // (start-address units of 16 bytes), so the single issuing thread keeps up with the
+          // tensor pipe
+          const uint32_t xa = smem_u32(smem + st * STAGE_BYTES);
+          const uint64_t xd0 = make_desc(xa), ed0 = make_desc(xa + HALF_BYTES);
 #pragma unroll
           for (int s = 1; s <= KS; ++s) {
 #pragma unroll
@@ -988,8 +992,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
               const uint32_t dacc = tmem + (uint32_t)(a * 128);
 #pragma unroll
               for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t xd = make_desc(xa + (uint32_t)((t - 1) * SLICE_BYTES) + ks * KSTEP_BYTES);
-                const uint64_t ed = make_desc(ea + (uint32_t)((s - 1) * SLICE_BYTES) + ks * KSTEP_BYTES);
+                const uint64_t xd = xd0 + (uint64_t)((((t - 1) * SLICE_BYTES) + ks * KSTEP_BYTES) >> 4);
+                const uint64_t ed = ed0 + (uint64_t)((((s - 1) * SLICE_BYTES) + ks * KSTEP_BYTES) >> 4);
                 if (TRANS)
                   mma_bf16(dacc, xd, ed, idesc, init[a] ? 1u : 0u);
                 else
@@ -1056,6 +1060,377 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ---------------------------------------------------------------- double-buffered variant
+// Tiles of 128 E rows x 64 fibers with E as the A operand (M = 128) and the fibers' digit
+// slices as B (N = 64) in both orientations, so that one tile's four level accumulators take
+// 4 x 64 TMEM columns and two tiles alternate between columns [0, 256) and [256, 512): the
+// epilogue drains tile t while the MMAs of tile t+1 run.  Same roles as the warp-specialised
+// kernel (8 producer, 4 epilogue, 1 MMA, 1 scheduler warp).  Producers hold three chunks
+// (8 values a thread each) in registers, so the loads of chunk c+2 are in flight while chunk c
+// is cut.  With fibers on the TMEM columns, a transposed pass's outputs (fiber = fastest
+// index) are staged in shared memory and written back row by row, coalesced.  Every job of a
+// pass needs n >= 64 (two or more 32-wide chunks).
+constexpr int DB_XSLICE = 64 * KC * 2;       // one slice of a 64-fiber chunk: 4 KB
+constexpr int DB_STAGE_PITCH = 528;          // bytes per staged output row (64 x 8 B + 16)
+constexpr int DB_STAGE_BYTES = 128 * DB_STAGE_PITCH;
+
+size_t db_smem_bytes(int ks) {
+  return (size_t)2 * ks * (DB_XSLICE + SLICE_BYTES) + DB_STAGE_BYTES + WS_BAR_BYTES + WS_SLOT_BYTES + 32;
+}
+
+// 8 consecutive values (k = kc .. kc+7) of fiber g0 + fib
+template <bool IN_F64, bool TRANS>
+__device__ __forceinline__ void db_load(const WsSlot& S, int fib, int kc, Raw<IN_F64>& raw) {
+  const long long gr = S.g0 + fib;
+  const bool vr = TRANS ? (gr < S.R) : (gr < S.B0);
+  if (!TRANS && !IN_F64) {
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const int k = kc + e;
+      const bool ok = vr && k < S.n;
+      const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(S.in) +
+                                                                   gr * (long long)S.n + k))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      raw.f[e] = make_float2(v.x, v.y);
+      raw.f[e + 1] = make_float2(v.z, v.w);
+    }
+    return;
+  }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int k = kc + e;
+    const bool ok = vr && k < S.n;
+    const long long idx = TRANS ? S.base + (long long)k * S.R + gr : gr * (long long)S.n + k;
+    if (IN_F64)
+      raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(S.in) + idx) : 0.0;
+    else
+      raw.f[e] = ok ? __ldg(reinterpret_cast<const float2*>(S.in) + idx) : make_float2(0.f, 0.f);
+  }
+}
+
+template <int KS, bool IN_F64, bool TRANS>
+__global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_constant__ GPass P, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int XBYTES = KS * DB_XSLICE;
+  constexpr int STAGE = XBYTES + KS * SLICE_BYTES;
+  uint8_t* staging = smem + 2 * STAGE;
+  uint8_t* tail = staging + DB_STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
+  uint64_t* full_x = bars;          // [2]
+  uint64_t* full_e = bars + 2;      // [2]
+  uint64_t* empty = bars + 4;       // [2]
+  uint64_t* tmem_full = bars + 6;   // [2] one per TMEM buffer
+  uint64_t* tmem_empty = bars + 8;  // [2]
+  uint64_t* done = bars + 10;
+  uint64_t* slot_full = bars + 11;  // [WS_SLOTS]
+  uint64_t* slot_empty = bars + 15; // [WS_SLOTS]
+  WsSlot* slots = reinterpret_cast<WsSlot*>(tail + WS_BAR_BYTES);
+  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(tail + WS_BAR_BYTES + WS_SLOT_BYTES);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(tail + WS_BAR_BYTES + WS_SLOT_BYTES + 16);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long total_tiles = P.total_tiles;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_x[q])), "r"(WS_PROD));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_e[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tmem_full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tmem_empty[q])), "r"(WS_EPI));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
+    for (int q = 0; q < WS_SLOTS; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&slot_empty[q])), "r"(WS_SLOT_READERS));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *abort_s = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_s)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_s;
+
+  if (warp < WS_EPI0) {
+    // ------------------------------------------------------------ producers
+    const int fib = tid & 63;   // fiber of the tile
+    const int kg = tid >> 6;    // k-group (8 values) of every 32-wide chunk
+    uint32_t it = 0, tc = 0;
+    int e_last = -1;            // thread 0: chunk of the latest E bulk copy
+    long long tile = blockIdx.x;
+    WsSlot S, Sn;
+    Raw<IN_F64> r0, r1, r2;     // chunks it, it+1 and (in flight) it+2
+    bool have = false;
+    if (tile < total_tiles) {
+      have = ws_get(slots, slot_full, slot_empty, 0, S);
+      if (!have) ws_fail(abort_s, status);
+    }
+    if (have) {
+      db_load<IN_F64, TRANS>(S, fib, 8 * kg, r0);
+      db_load<IN_F64, TRANS>(S, fib, 32 + 8 * kg, r1);
+    }
+    bool stop = false;
+    for (; have && tile < total_tiles; tile += gridDim.x, ++tc) {
+      const int nchunks = S.nsub;
+      const int eb = 1011 + S.eX;
+      const float xsc = pow2f_full(-S.eX);
+      const bool has_next = tile + gridDim.x < total_tiles;
+      bool have_next = false;
+      for (int c = 0; c < nchunks; ++c, ++it) {
+        const uint32_t st = it & 1u, use = it >> 1;
+        uint8_t* sX = smem + st * STAGE;
+        uint8_t* sE = sX + XBYTES;
+        // chunk it + 2 in flight before the wait for a free stage
+        if (c + 2 < nchunks) {
+          db_load<IN_F64, TRANS>(S, fib, 32 * (c + 2) + 8 * kg, r2);
+        } else {
+          if (c + 2 == nchunks && has_next) {
+            have_next = ws_get(slots, slot_full, slot_empty, tc + 1, Sn);
+            if (!have_next) ws_fail(abort_s, status);
+          }
+          if (have_next) db_load<IN_F64, TRANS>(Sn, fib, 32 * (c + 2 - nchunks) + 8 * kg, r2);
+        }
+        if (use >= 1 && !mbar_wait(smem_u32(&empty[st]), (use - 1) & 1u)) ws_fail(abort_s, status);
+        if (*abort_s) { stop = true; break; }
+        if (tid == 0) {
+          e_last = (int)it;
+          mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)(KS * SLICE_BYTES));
+          bulk_copy_g2s(smem_u32(sE), S.ebase + (size_t)c * KS * SLICE_BYTES, (uint32_t)(KS * SLICE_BYTES),
+                        smem_u32(&full_e[st]));
+        }
+        uint32_t pk[KS][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          if (IN_F64) {
+            uint32_t s0, s1;
+            const uint64_t F0 = round_digits<KS>(fixed_f64(r0.d[e], eb, s0));
+            const uint64_t F1 = round_digits<KS>(fixed_f64(r0.d[e + 1], eb, s1));
+            uint32_t w[KS];
+            cut_pair<KS>(F0, s0, F1, s1, w);
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
+          } else {
+            float v0[KS], v1[KS];
+            cut_ff_float<KS>(r0.f[e].x, r0.f[e].y, xsc, v0);
+            cut_ff_float<KS>(r0.f[e + 1].x, r0.f[e + 1].y, xsc, v1);
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v0[sl], v1[sl]);
+          }
+        }
+        const uint32_t off = chunk_offset(fib, kg);
+#pragma unroll
+        for (int sl = 0; sl < KS; ++sl)
+          *reinterpret_cast<uint4*>(sX + sl * DB_XSLICE + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&full_x[st]));
+        r0 = r1;
+        r1 = r2;
+      }
+      if (stop) break;
+      S = Sn;
+    }
+    if (tid == 0 && *abort_s) {
+      // bulk copies still in flight must land before the CTA's shared memory is released
+      for (int k = e_last; k >= 0 && k >= e_last - 1; --k)
+        mbar_wait(smem_u32(&full_e[k & 1]), ((uint32_t)k >> 1) & 1u);
+    }
+  } else if (warp < WS_MMA) {
+    // ------------------------------------------------------------ epilogue
+    const int q4 = warp - WS_EPI0;     // TMEM lane quarter (= warp % 4)
+    const int i = q4 * 32 + lane;      // E row of this thread (TMEM lane)
+    uint32_t tc = 0;
+    for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++tc) {
+      const uint32_t b = tc & 1u, u = tc >> 1;
+      WsSlot S;
+      bool ok = ws_get(slots, slot_full, slot_empty, tc, S);
+      ok = ok && mbar_wait(smem_u32(&tmem_full[b]), u & 1u);
+      if (!ok) ws_fail(abort_s, status);
+      // every epilogue thread decides alike; the vote is also the barrier that frees the
+      // staging area of the previous tile
+      if (epi_vote_any(!ok || *abort_s)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tb = tmem + 256u * b + ((uint32_t)(q4 * 32) << 16);
+      const bool vi = i < S.nrows_e;
+      const float sc = pow2f(S.eX + (vi ? __ldg(S.rexp + i) : 0));
+      const int ncols = TRANS ? (int)min(64LL, S.R - S.g0) : (int)min(64LL, S.B0 - S.g0);
+      const bool f64 = S.out_f64 != 0;
+      uint32_t mx = 0;
+      for (int cc = 0; cc < ncols; cc += 16) {
+        float d2[16], d3[16], d4[16], d5[16];
+        tmem_ld16(tb + (uint32_t)cc, d2);
+        tmem_ld16(tb + 64u + (uint32_t)cc, d3);
+        tmem_ld16(tb + 128u + (uint32_t)cc, d4);
+        if (KS >= 4) tmem_ld16(tb + 192u + (uint32_t)cc, d5);
+        tmem_wait_ld();
+        float hs[16], ls[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hs[j], ls[j]);
+          hs[j] *= sc;
+          ls[j] *= sc;
+          mx = max(mx, __float_as_uint(hs[j]) & 0x7FFFFFFFu);
+        }
+        if (TRANS) {
+          // row i of the staged tile: 16 columns as 8 pairs of 16 bytes
+          uint8_t* row = staging + i * DB_STAGE_PITCH + cc * 8;
+          if (!f64) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 2)
+              *reinterpret_cast<float4*>(row + j * 8) = make_float4(hs[j], ls[j], hs[j + 1], ls[j + 1]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; j += 2)
+              *reinterpret_cast<double2*>(row + j * 8) =
+                  make_double2(ff_to_f64(hs[j], ls[j]), ff_to_f64(hs[j + 1], ls[j + 1]));
+          }
+        } else if (vi) {
+          const int jn = ncols - cc;  // >= 16 unless this is the tile's last group
+          const long long o = (S.g0 + cc) * (long long)S.n + 128 * S.rb + i;
+          if (!f64) {
+            float2* dst = reinterpret_cast<float2*>(S.out) + o;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (j < jn) dst[(long long)j * S.n] = make_float2(hs[j], ls[j]);
+          } else {
+            double* dst = reinterpret_cast<double*>(S.out) + o;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (j < jn) dst[(long long)j * S.n] = ff_to_f64(hs[j], ls[j]);
+          }
+        }
+      }
+      // the accumulators of buffer b are free for tile t+2
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&tmem_empty[b]));
+      if (TRANS) {
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // the staged tile is complete
+        // rows q4, q4+4, ...: 64 consecutive fibers = 512 contiguous bytes in the output
+        const int nrows = S.nrows_e;
+        for (int r = q4; r < nrows; r += 4) {
+          const int c2 = 2 * lane;  // this lane's column pair
+          if (c2 < ncols) {
+            const long long o = S.base + (long long)(128 * S.rb + r) * S.R + S.g0 + c2;
+            const uint8_t* src = staging + r * DB_STAGE_PITCH + c2 * 8;
+            if (!f64) {
+              *reinterpret_cast<float4*>(reinterpret_cast<float2*>(S.out) + o) = *reinterpret_cast<const float4*>(src);
+            } else {
+              // the caller's float64 buffer need only be 8-byte aligned
+              const double2 v = *reinterpret_cast<const double2*>(src);
+              double* dst = reinterpret_cast<double*>(S.out) + o;
+              dst[0] = v.x;
+              dst[1] = v.y;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      // |v| < 2^{biased - 126}; a zero vector keeps the slot's initial (very negative) value
+      const int emax = (int)(mx >> 23);
+      if (lane == 0 && S.out_exp && emax > 0) atomicMax(S.out_exp, emax - 126);
+    }
+  } else if (warp == WS_MMA) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- MMA issuer
+      uint32_t it = 0, tc = 0;
+      bool issued = false;
+      const uint32_t idesc = make_idesc(128, 64);
+      for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++tc) {
+        const uint32_t b = tc & 1u, u = tc >> 1;
+        WsSlot S;
+        if (!ws_get(slots, slot_full, slot_empty, tc, S)) ws_fail(abort_s, status);
+        if (u >= 1 && !mbar_wait(smem_u32(&tmem_empty[b]), (u - 1) & 1u)) ws_fail(abort_s, status);
+        if (*abort_s) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool init[4] = {false, false, false, false};
+        bool stop = false;
+        for (int c = 0; c < S.nsub; ++c, ++it) {
+          const uint32_t st = it & 1u, use = it >> 1;
+          if (!mbar_wait(smem_u32(&full_x[st]), use & 1u) || !mbar_wait(smem_u32(&full_e[st]), use & 1u))
+            ws_fail(abort_s, status);
+          if (*abort_s) { stop = true; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t xa = smem_u32(smem + st * STAGE);
+          const uint64_t xd0 = make_desc(xa), ed0 = make_desc(xa + XBYTES);
+          const uint32_t acc0 = tmem + 256u * b;
+#pragma unroll
+          for (int s = 1; s <= KS; ++s) {
+#pragma unroll
+            for (int t = 1; t <= KS; ++t) {
+              if (s + t > KS + 1) continue;
+              const int L = s + t - 2;
+              const int a = L < 3 ? L : 3;
+#pragma unroll
+              for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t ed = ed0 + (uint64_t)((((s - 1) * SLICE_BYTES) + ks * KSTEP_BYTES) >> 4);
+                const uint64_t xd = xd0 + (uint64_t)((((t - 1) * DB_XSLICE) + ks * KSTEP_BYTES) >> 4);
+                mma_bf16(acc0 + (uint32_t)(a * 64), ed, xd, idesc, init[a] ? 1u : 0u);
+                init[a] = true;
+                issued = true;
+              }
+            }
+          }
+          mma_commit(smem_u32(&empty[st]));
+        }
+        if (stop) break;
+        mma_commit(smem_u32(&tmem_full[b]));
+      }
+      // every MMA this thread issued is complete before TMEM is released
+      mma_commit(smem_u32(done));
+      if (issued) mbar_wait(smem_u32(done), 0u);
+    }
+  } else if (warp == WS_SCHED && lane == 0) {
+    // ------------------------------------------------------------ scheduler (64-fiber tiles)
+    int job = 0;
+    uint32_t tc = 0;
+    for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++tc) {
+      const uint32_t q = tc % WS_SLOTS;
+      if (tc >= WS_SLOTS && !mbar_wait(smem_u32(&slot_empty[q]), ((tc / WS_SLOTS) - 1) & 1u))
+        ws_fail(abort_s, status);
+      if (*abort_s) break;
+      int lo = job, hi = P.njobs - 1;  // tiles of this CTA increase: the job index only moves forward
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.jobs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+      }
+      job = lo;
+      const GJob& J = P.jobs[job];
+      const long long tj = tile - J.tile_begin;
+      const long long rt = TRANS ? (J.R + 63) / 64 : 1;
+      const long long per_rb = TRANS ? J.B0 * rt : (J.B0 + 63) / 64;
+      const int rb = (int)(tj / per_rb);
+      const long long th = tj % per_rb;
+      WsSlot& S = slots[q];
+      S.in = (J.in_tab >= 0) ? (const void*)((const char*)P.ptrtab[J.in_tab] + J.tab_off_in) : J.in;
+      S.out = (J.out_tab >= 0) ? (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out) : J.out;
+      const int nsub = (J.n + 31) / 32;
+      S.ebase = J.eslices + (size_t)rb * (size_t)nsub * KS * SLICE_BYTES;
+      S.rexp = J.rexp + 128 * rb;
+      S.out_exp = J.out_exp;
+      S.R = J.R;
+      S.B0 = J.B0;
+      S.base = TRANS ? (th / rt) * (long long)J.n * J.R : 0;
+      S.g0 = TRANS ? (th % rt) * 64 : th * 64;
+      S.n = J.n;
+      S.nsub = nsub;
+      S.rb = rb;
+      const int eX = *J.in_exp;
+      S.eX = eX < -600 ? 0 : eX;  // all-zero input
+      S.nrows_e = min(128, J.n - 128 * rb);
+      S.out_f64 = J.out_f64;
+      mbar_arrive(smem_u32(&slot_full[q]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 __global__ void ptrtab_set_kernel(void** tab, PtrArgs args) {
   const int i = threadIdx.x;
   if (i < args.n) tab[i] = args.p[i];
@@ -1096,9 +1471,43 @@ int launch_ks(const GPass& P, bool in_f64, bool trans, int grid, bool ws, int* s
                : launch_one<KS, SUB, false, false>(P, grid, ws, status, st);
 }
 
+template <int KS, bool IN_F64, bool TRANS>
+int launch_db(const GPass& P, int grid, int* status, cudaStream_t st) {
+  const size_t sm = db_smem_bytes(KS);
+  auto kern = mode_kernel_db<KS, IN_F64, TRANS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) {
+    set_error(std::string("tc mode kernel smem attribute: ") + cudaGetErrorString(e));
+    return PHIKRON_ECUDA;
+  }
+  launch_begin(KC_TC_MODE, st);
+  kern<<<grid, WS_THREADS, sm, st>>>(P, status);
+  launch_end(st);
+  PK_CHECK_LAUNCH();
+  return PHIKRON_OK;
+}
+
+template <int KS>
+int launch_db_ks(const GPass& P, bool in_f64, bool trans, int grid, int* status, cudaStream_t st) {
+  if (in_f64)
+    return trans ? launch_db<KS, true, true>(P, grid, status, st) : launch_db<KS, true, false>(P, grid, status, st);
+  return trans ? launch_db<KS, false, true>(P, grid, status, st) : launch_db<KS, false, false>(P, grid, status, st);
+}
+
 int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) {
   if (P.njobs <= 0 || P.total_tiles <= 0) return PHIKRON_OK;
   const int grid = (int)std::min<long long>(P.total_tiles, S.grid);
+  if (S.db) {
+    switch (S.slices) {
+      case 3: return launch_db_ks<3>(P, S.in_f64, S.trans, grid, status, st);
+      case 4: return launch_db_ks<4>(P, S.in_f64, S.trans, grid, status, st);
+      case 5: return launch_db_ks<5>(P, S.in_f64, S.trans, grid, status, st);
+      case 6: return launch_db_ks<6>(P, S.in_f64, S.trans, grid, status, st);
+      default: break;
+    }
+    set_error("tc mode pass: unsupported slice count");
+    return PHIKRON_EINVAL;
+  }
   if (S.sub == 1) {
     switch (S.slices) {
       case 3: return launch_ks<3, 1>(P, S.in_f64, S.trans, grid, S.ws, status, st);
