@@ -132,9 +132,9 @@ def peaks():
 
 # DRAM traffic of the tensor-core mode kernel from the ncu capture summarised in
 # profiles/mode_kernel_ws_convdiff3d_n128_ncu_full.md (one launch of the z-mode node pass:
-# 9 vectors x N unknowns); valid only while the kernel source is the one captured.
-PROFILED_MODE_TRAFFIC = {"source_sha256_16": "24582c6a013f2f9d", "bytes": 152.646912e6 + 96.140288e6,
-                         "vector_passes": 9, "N": 2097152}
+# 11 vectors x N unknowns); valid only while the kernel source is the one captured.
+PROFILED_MODE_TRAFFIC = {"source_sha256_16": "5f383dad0f2a4c52", "bytes": 186.0928e6 + 128.35712e6,
+                         "vector_passes": 11, "N": 2097152}
 
 
 def mode_traffic_per_launch(N, vector_passes_per_launch):
