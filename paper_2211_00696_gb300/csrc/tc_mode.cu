@@ -31,12 +31,14 @@
 //       A = E (128 rows, zero-padded), B = X tile (128 rows).  TMEM lane = i, column = row;
 //       stores out[row][i] coalesced over lanes.
 // K (= n) is processed in chunks of 32 through a 2-stage shared-memory ring: while the
-// tensor cores work on chunk c, 512 threads cut chunk c+1 (four threads per operand row,
-// 8 k each, with the raw values of the following chunk -- or of the next tile's first
-// chunk -- already in flight), and the E slices of the chunk arrive by one asynchronous
-// bulk copy (TMA) per chunk.  Operands use the
-// no-swizzle K-major canonical layout (8-row x 16-byte core matrices; LBO = 128 B between
-// core matrices along K, SBO = 512 B between 8-row groups).
+// tensor cores work on chunk c, the producer threads cut chunk c+1 (with the raw values of
+// the following chunk -- or of the next tile's first chunk -- already in flight), and the E
+// slices of the chunk arrive by one asynchronous bulk copy (TMA) per chunk.  Operands use
+// the 64-byte-swizzled K-major layout (one 64-byte row of 32 BF16 per operand row, its four
+// 16-byte pieces permuted by bits 1-2 of the row; SBO = 512 B between 8-row groups); the
+// no-swizzle canonical layout (8-row x 16-byte core matrices, LBO = 128 B) remains
+// selectable through kSwizzle64.  The warp-specialised and double-buffered variants below
+// are the ones the library launches by default.
 //
 // Every wait on an mbarrier is bounded; on expiry the kernel records PHIKRON_ETIMEOUT in the
 // status word, waits (bounded) for its own tensor-core work, frees its TMEM and returns.
@@ -93,6 +95,55 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t 
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+// The descriptor's high word (SBO, version, layout type) is the same for every operand of these
+// kernels; only the start-address field of the low word moves.  Shared-memory addresses stay
+// below 256 KB, so an offset added to the low word never carries out of that 14-bit field.
+constexpr uint32_t DESC_HI = kSwizzle64 ? ((512u >> 4) | (1u << 14) | (4u << 29)) : ((512u >> 4) | (1u << 14));
+constexpr uint32_t DESC_LBO = kSwizzle64 ? (1u << 16) : ((128u >> 4) << 16);
+
+__device__ __forceinline__ uint32_t desc_lo(uint32_t saddr) { return ((saddr >> 4) & 0x3FFFu) | DESC_LBO; }
+
+// one MMA from two descriptor low words; `accumulate` is a compile-time constant at every call
+// site after unrolling, so the issue loop carries no per-MMA select or 64-bit arithmetic
+__device__ __forceinline__ void mma_bf16_lo(uint32_t tmem_d, uint32_t a_lo, uint32_t b_lo, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .b64 da, db;\n.reg .b32 hi;\n.reg .pred p;\n"
+      "mov.b32 hi, %4;\nmov.b64 da, {%1, hi};\nmov.b64 db, {%2, hi};\n"
+      "setp.ne.b32 p, %5, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(a_lo), "r"(b_lo), "r"(idesc), "n"(DESC_HI), "r"(accumulate));
+}
+
+// The slice-pair MMAs of one 32-wide K chunk: pairs (s, t) with s + t <= KS + 1, two K-steps
+// each, level s + t - 2 into accumulator min(level, 3) (ACC_COLS columns apart).  FIRST: the
+// tile's first chunk, where each accumulator's first MMA overwrites it -- the first touch of
+// accumulator a is pair (1, a + 1) at K-step 0.  E_IS_A puts E in the A operand (M = output
+// rows) and the input slices in B; otherwise the input slices are A.  XSLICE: bytes between
+// input slices.
+template <int KS, bool FIRST, bool E_IS_A, int ACC_COLS, int XSLICE>
+__device__ __forceinline__ void issue_chunk(uint32_t acc0, uint32_t xlo, uint32_t elo, uint32_t idesc) {
+#pragma unroll
+  for (int s = 1; s <= KS; ++s) {
+#pragma unroll
+    for (int t = 1; t <= KS; ++t) {
+      if (s + t > KS + 1) continue;
+      const int L = s + t - 2;
+      const int a = L < 3 ? L : 3;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint32_t xd = xlo + (uint32_t)((((t - 1) * XSLICE) + ks * KSTEP_BYTES) >> 4);
+        const uint32_t ed = elo + (uint32_t)((((s - 1) * SLICE_BYTES) + ks * KSTEP_BYTES) >> 4);
+        const uint32_t accumulate = (FIRST && s == 1 && ks == 0 && t <= 4) ? 0u : 1u;
+        if (E_IS_A)
+          mma_bf16_lo(acc0 + (uint32_t)(a * ACC_COLS), ed, xd, idesc, accumulate);
+        else
+          mma_bf16_lo(acc0 + (uint32_t)(a * ACC_COLS), xd, ed, idesc, accumulate);
+      }
+    }
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -969,7 +1020,6 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
         if (*abort_s) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t idesc = TRANS ? make_idesc(128, S.nrows_e) : make_idesc(128, 128);
-        bool init[4] = {false, false, false, false};
         bool stop = false;
         for (int c = 0; c < S.nsub; ++c, ++it) {
           const uint32_t st = it & 1u, use = it >> 1;
@@ -978,31 +1028,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
           if (*abort_s) { stop = true; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           // descriptors built once per chunk; the issue loop only adds compile-time offsets
-          // (start-address units of 16 bytes), so the single issuing thread keeps up with the
-          // tensor pipe
+          // (start-address units of 16 bytes) to 32-bit low words, so the single issuing thread
+          // keeps up with the tensor pipe
           const uint32_t xa = smem_u32(smem + st * STAGE_BYTES);
-          const uint64_t xd0 = make_desc(xa), ed0 = make_desc(xa + HALF_BYTES);
-#pragma unroll
-          for (int s = 1; s <= KS; ++s) {
-#pragma unroll
-            for (int t = 1; t <= KS; ++t) {
-              if (s + t > KS + 1) continue;
-              const int L = s + t - 2;
-              const int a = L < 3 ? L : 3;
-              const uint32_t dacc = tmem + (uint32_t)(a * 128);
-#pragma unroll
-              for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t xd = xd0 + (uint64_t)((((t - 1) * SLICE_BYTES) + ks * KSTEP_BYTES) >> 4);
-                const uint64_t ed = ed0 + (uint64_t)((((s - 1) * SLICE_BYTES) + ks * KSTEP_BYTES) >> 4);
-                if (TRANS)
-                  mma_bf16(dacc, xd, ed, idesc, init[a] ? 1u : 0u);
-                else
-                  mma_bf16(dacc, ed, xd, idesc, init[a] ? 1u : 0u);
-                init[a] = true;
-                issued = true;
-              }
-            }
-          }
+          const uint32_t xlo = desc_lo(xa), elo = desc_lo(xa + HALF_BYTES);
+          if (c == 0)
+            issue_chunk<KS, true, !TRANS, 128, SLICE_BYTES>(tmem, xlo, elo, idesc);
+          else
+            issue_chunk<KS, false, !TRANS, 128, SLICE_BYTES>(tmem, xlo, elo, idesc);
+          issued = true;
           mma_commit(smem_u32(&empty[st]));
         }
         if (stop) break;
@@ -1347,7 +1381,6 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
         if (u >= 1 && !mbar_wait(smem_u32(&tmem_empty[b]), (u - 1) & 1u)) ws_fail(abort_s, status);
         if (*abort_s) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        bool init[4] = {false, false, false, false};
         bool stop = false;
         for (int c = 0; c < S.nsub; ++c, ++it) {
           const uint32_t st = it & 1u, use = it >> 1;
@@ -1356,25 +1389,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
           if (*abort_s) { stop = true; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t xa = smem_u32(smem + st * STAGE);
-          const uint64_t xd0 = make_desc(xa), ed0 = make_desc(xa + XBYTES);
+          const uint32_t xlo = desc_lo(xa), elo = desc_lo(xa + XBYTES);
           const uint32_t acc0 = tmem + 256u * b;
-#pragma unroll
-          for (int s = 1; s <= KS; ++s) {
-#pragma unroll
-            for (int t = 1; t <= KS; ++t) {
-              if (s + t > KS + 1) continue;
-              const int L = s + t - 2;
-              const int a = L < 3 ? L : 3;
-#pragma unroll
-              for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t ed = ed0 + (uint64_t)((((s - 1) * SLICE_BYTES) + ks * KSTEP_BYTES) >> 4);
-                const uint64_t xd = xd0 + (uint64_t)((((t - 1) * DB_XSLICE) + ks * KSTEP_BYTES) >> 4);
-                mma_bf16(acc0 + (uint32_t)(a * 64), ed, xd, idesc, init[a] ? 1u : 0u);
-                init[a] = true;
-                issued = true;
-              }
-            }
-          }
+          if (c == 0)
+            issue_chunk<KS, true, true, 64, DB_XSLICE>(acc0, xlo, elo, idesc);
+          else
+            issue_chunk<KS, false, true, 64, DB_XSLICE>(acc0, xlo, elo, idesc);
+          issued = true;
           mma_commit(smem_u32(&empty[st]));
         }
         if (stop) break;
