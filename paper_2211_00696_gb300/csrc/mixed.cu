@@ -96,14 +96,6 @@ __device__ __forceinline__ double ff_to_f64(float hi, float lo) {
   return __longlong_as_double((long long)bits);
 }
 
-__device__ __forceinline__ int exp_plus1(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFF) - 126; }
-
-__device__ __forceinline__ void warp_max_atomic(int v, int* slot) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0 && slot && v > -1000) atomicMax(slot, v);
-}
-
 constexpr int MAXP = 8;
 constexpr int MAXM = 64;
 constexpr int EW_THREADS = 256;
@@ -154,122 +146,199 @@ __device__ __forceinline__ void st_pair(void* out, void* out2, bool f64, long lo
   emax = max(emax, (int)((__float_as_uint(b.x) >> 23) & 0xFFu));
 }
 
-// y_j = sum_k coef[j][k] T_k in float-float (Algorithm 1, second step), grouped over jobs
-template <int P_>
-__global__ void __launch_bounds__(EW_THREADS) g_weighted_kernel(const EJob* __restrict__ jobs, int njobs,
-                                                                const void* const* ptrtab) {
-  __shared__ float2 cs[P_ * MAXM];
-  const int jb = find_ejob(jobs, njobs, blockIdx.x);
-  const EJob& J = jobs[jb];
-  const int m = J.m;
-  for (int i = threadIdx.x; i < P_ * m; i += EW_THREADS) cs[i] = J.coef[i];
+// Exponent slots: the block's largest biased exponent per output (0 = nothing stored; BIAS
+// 126 for FP32 exponent fields, 1022 for float64 ones, so that |v| < 2^{emax - BIAS}),
+// reduced over warps in shared memory, then one atomicMax per output and block (instead of
+// one per warp: same-address atomics serialise in L2).  Called by every thread of the block.
+template <int P_, int BIAS = 126>
+__device__ __forceinline__ void block_exp_flush(int (&emax)[P_], int* out_exp, int (*red)[EW_THREADS / 32]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < P_; ++j) {
+    int v = emax[j] > 0 ? emax[j] - BIAS : -1000;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[j][warp] = v;
+    emax[j] = 0;
+  }
   __syncthreads();
-  void* out = tab_ptr(ptrtab, J.out_tab, J.tab_off_out, J.out);
-  void* out2 = tab_ptr(ptrtab, J.out2_tab, J.tab_off_out2, J.out2);
-  const bool f64 = J.out_f64 != 0;
-  const long long N = J.N, stride = J.stride;
+  if (threadIdx.x < P_ && out_exp) {
+    int v = -1000;
+#pragma unroll
+    for (int w = 0; w < EW_THREADS / 32; ++w) v = max(v, red[threadIdx.x][w]);
+    if (v > -1000) atomicMax(out_exp + threadIdx.x, v);
+  }
+  __syncthreads();
+}
+
+// The elementwise kernels run a grid of (SMs x resident blocks) that strides over the
+// launch's virtual blocks of EW_BLOCK elements (all jobs laid end to end), so that no
+// partial second wave idles most of the GPU.
+
+// y_j = sum_k coef[j][k] T_k in float-float (Algorithm 1, second step), grouped over jobs.
+// The T_k of a pair are read in batches (KB) before any arithmetic, so that each thread keeps
+// KB x 16 bytes of loads in flight.
+template <int P_>
+__global__ void __launch_bounds__(EW_THREADS, P_ <= 3 ? 4 : 3) g_weighted_kernel(const EJob* __restrict__ jobs,
+                                                                                 int njobs, long long total,
+                                                                                 const void* const* ptrtab) {
+  constexpr int KB = P_ <= 3 ? 6 : 4;  // T_k per batch (register budget without spills)
+  __shared__ float2 cs[P_ * MAXM];
+  __shared__ int red[P_][EW_THREADS / 32];
   int emax[P_];
 #pragma unroll
   for (int j = 0; j < P_; ++j) emax[j] = 0;
-  const long long base = (blockIdx.x - J.block_begin) * EW_BLOCK;
+  int cur = -1;
+  for (long long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int jb = find_ejob(jobs, njobs, vb);  // uniform over the block
+    const EJob& J = jobs[jb];
+    if (jb != cur) {
+      if (cur >= 0) block_exp_flush<P_>(emax, jobs[cur].out_exp, red);
+      for (int q = threadIdx.x; q < P_ * J.m; q += EW_THREADS) cs[q] = J.coef[q];
+      __syncthreads();
+      cur = jb;
+    }
+    const int m = J.m;
+    void* out = tab_ptr(ptrtab, J.out_tab, J.tab_off_out, J.out);
+    void* out2 = tab_ptr(ptrtab, J.out2_tab, J.tab_off_out2, J.out2);
+    const bool f64 = J.out_f64 != 0;
+    const long long N = J.N, stride = J.stride;
+    const long long base = (vb - J.block_begin) * EW_BLOCK;
+#pragma unroll 1
+    for (int e = 0; e < EW_PAIRS; ++e) {
+      const long long i = base + 2 * ((long long)e * EW_THREADS + threadIdx.x);
+      if (i < N) {
+        float2 acc0[P_], acc1[P_];
 #pragma unroll
-  for (int e = 0; e < EW_PAIRS; ++e) {
-    const long long i = base + 2 * ((long long)e * EW_THREADS + threadIdx.x);
-    if (i < N) {
-      float2 acc0[P_], acc1[P_];
+        for (int j = 0; j < P_; ++j) acc0[j] = acc1[j] = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int k0 = 0; k0 < m; k0 += KB) {
+          float2 t0[KB], t1[KB];
 #pragma unroll
-      for (int j = 0; j < P_; ++j) acc0[j] = acc1[j] = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int k = 0; k < m; ++k) {
-        float2 t0, t1;
-        ld_pair(J.a + k * stride + i, t0, t1);
+          for (int q = 0; q < KB; ++q)
+            if (k0 + q < m) ld_pair(J.a + (k0 + q) * stride + i, t0[q], t1[q]);
 #pragma unroll
-        for (int j = 0; j < P_; ++j) {
-          ff_fma(acc0[j], cs[j * m + k], t0);
-          ff_fma(acc1[j], cs[j * m + k], t1);
+          for (int q = 0; q < KB; ++q) {
+            if (k0 + q < m) {
+#pragma unroll
+              for (int j = 0; j < P_; ++j) {
+                ff_fma(acc0[j], cs[j * m + k0 + q], t0[q]);
+                ff_fma(acc1[j], cs[j * m + k0 + q], t1[q]);
+              }
+            }
+          }
         }
-      }
 #pragma unroll
-      for (int j = 0; j < P_; ++j) st_pair(out, out2, f64, j * stride + i, acc0[j], acc1[j], emax[j]);
+        for (int j = 0; j < P_; ++j) st_pair(out, out2, f64, j * stride + i, acc0[j], acc1[j], emax[j]);
+      }
     }
   }
-  if (J.out_exp) {
-#pragma unroll
-    for (int j = 0; j < P_; ++j) warp_max_atomic(emax[j] > 0 ? emax[j] - 126 : -1000, J.out_exp + j);
-  }
+  if (cur >= 0) block_exp_flush<P_>(emax, jobs[cur].out_exp, red);
 }
 
 // y-hat_i = 2^{-i}(Z_i + sum_{j<=i} y_j/(i-j)!), i = 1..p (Eq. (29)), grouped over jobs
 template <int P_>
-__global__ void __launch_bounds__(EW_THREADS) g_squaring_kernel(const EJob* __restrict__ jobs, int njobs,
-                                                                const void* const* ptrtab, InvFact inv) {
-  const int jb = find_ejob(jobs, njobs, blockIdx.x);
-  const EJob& J = jobs[jb];
-  void* out = tab_ptr(ptrtab, J.out_tab, J.tab_off_out, J.out);
-  void* out2 = tab_ptr(ptrtab, J.out2_tab, J.tab_off_out2, J.out2);
-  const bool f64 = J.out_f64 != 0;
-  const long long N = J.N, stride = J.stride;
+__global__ void __launch_bounds__(EW_THREADS, 4) g_squaring_kernel(const EJob* __restrict__ jobs, int njobs,
+                                                                   long long total, const void* const* ptrtab,
+                                                                   InvFact inv) {
+  __shared__ int red[P_][EW_THREADS / 32];
   int emax[P_];
 #pragma unroll
   for (int j = 0; j < P_; ++j) emax[j] = 0;
-  const long long base = (blockIdx.x - J.block_begin) * EW_BLOCK;
+  int cur = -1;
+  for (long long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int jb = find_ejob(jobs, njobs, vb);
+    const EJob& J = jobs[jb];
+    if (jb != cur) {
+      if (cur >= 0) block_exp_flush<P_>(emax, jobs[cur].out_exp, red);
+      cur = jb;
+    }
+    void* out = tab_ptr(ptrtab, J.out_tab, J.tab_off_out, J.out);
+    void* out2 = tab_ptr(ptrtab, J.out2_tab, J.tab_off_out2, J.out2);
+    const bool f64 = J.out_f64 != 0;
+    const long long N = J.N, stride = J.stride;
+    const long long base = (vb - J.block_begin) * EW_BLOCK;
+#pragma unroll 1
+    for (int e = 0; e < EW_PAIRS; ++e) {
+      const long long x = base + 2 * ((long long)e * EW_THREADS + threadIdx.x);
+      if (x < N) {
+        float2 y0[P_], y1[P_], z0[P_], z1[P_];
 #pragma unroll
-  for (int e = 0; e < EW_PAIRS; ++e) {
-    const long long x = base + 2 * ((long long)e * EW_THREADS + threadIdx.x);
-    if (x < N) {
-      float2 y0[P_], y1[P_], z0[P_], z1[P_];
-#pragma unroll
-      for (int j = 0; j < P_; ++j) {
-        ld_pair(J.b + j * stride + x, y0[j], y1[j]);
-        ld_pair(J.a + j * stride + x, z0[j], z1[j]);
-      }
-      float sc = 1.0f;
-#pragma unroll
-      for (int q = 1; q <= P_; ++q) {
-        sc *= 0.5f;
-        float2 a0 = z0[q - 1], a1 = z1[q - 1];
-#pragma unroll
-        for (int j = 1; j <= q; ++j) {
-          const int d = q - j;
-          if (d <= 1) {
-            ff_add(a0, y0[j - 1]);
-            ff_add(a1, y1[j - 1]);
-          } else {
-            ff_fma(a0, inv.f[d], y0[j - 1]);
-            ff_fma(a1, inv.f[d], y1[j - 1]);
-          }
+        for (int j = 0; j < P_; ++j) {
+          ld_pair(J.b + j * stride + x, y0[j], y1[j]);
+          ld_pair(J.a + j * stride + x, z0[j], z1[j]);
         }
-        z0[q - 1] = make_float2(a0.x * sc, a0.y * sc);
-        z1[q - 1] = make_float2(a1.x * sc, a1.y * sc);
-      }
+        float sc = 1.0f;
 #pragma unroll
-      for (int q = 0; q < P_; ++q) st_pair(out, out2, f64, q * stride + x, z0[q], z1[q], emax[q]);
+        for (int q = 1; q <= P_; ++q) {
+          sc *= 0.5f;
+          float2 a0 = z0[q - 1], a1 = z1[q - 1];
+#pragma unroll
+          for (int j = 1; j <= q; ++j) {
+            const int d = q - j;
+            if (d <= 1) {
+              ff_add(a0, y0[j - 1]);
+              ff_add(a1, y1[j - 1]);
+            } else {
+              ff_fma(a0, inv.f[d], y0[j - 1]);
+              ff_fma(a1, inv.f[d], y1[j - 1]);
+            }
+          }
+          z0[q - 1] = make_float2(a0.x * sc, a0.y * sc);
+          z1[q - 1] = make_float2(a1.x * sc, a1.y * sc);
+        }
+#pragma unroll
+        for (int q = 0; q < P_; ++q) st_pair(out, out2, f64, q * stride + x, z0[q], z1[q], emax[q]);
+      }
     }
   }
-  if (J.out_exp) {
-#pragma unroll
-    for (int j = 0; j < P_; ++j) warp_max_atomic(emax[j] > 0 ? emax[j] - 126 : -1000, J.out_exp + j);
-  }
+  if (cur >= 0) block_exp_flush<P_>(emax, jobs[cur].out_exp, red);
 }
 
 // e with |v| < 2^e over a float64 vector (integer ops only), grouped over jobs
 __global__ void __launch_bounds__(EW_THREADS) g_expscan_kernel(const EJob* __restrict__ jobs, int njobs,
-                                                               const void* const* ptrtab) {
-  const int jb = find_ejob(jobs, njobs, blockIdx.x);
-  const EJob& J = jobs[jb];
-  const double* v = reinterpret_cast<const double*>(tab_ptr(ptrtab, J.v_tab, J.tab_off_v, (void*)J.v));
-  int e = -1000;
-  const long long base = (blockIdx.x - J.block_begin) * EW_BLOCK;
+                                                               long long total, const void* const* ptrtab) {
+  __shared__ int red[1][EW_THREADS / 32];
+  int emax[1] = {0};  // float64 exponent field: |v| < 2^{emax - 1022}
+  int cur = -1;
+  for (long long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int jb = find_ejob(jobs, njobs, vb);
+    const EJob& J = jobs[jb];
+    if (jb != cur) {
+      if (cur >= 0) block_exp_flush<1, 1022>(emax, jobs[cur].out_exp, red);
+      cur = jb;
+    }
+    const double* v = reinterpret_cast<const double*>(tab_ptr(ptrtab, J.v_tab, J.tab_off_v, (void*)J.v));
+    const long long base = (vb - J.block_begin) * EW_BLOCK;
+    uint64_t b[2 * EW_PAIRS];
 #pragma unroll
-  for (int q = 0; q < 2 * EW_PAIRS; ++q) {
-    const long long i = base + (long long)q * EW_THREADS + threadIdx.x;
-    if (i < J.N) {
-      const uint64_t b = (uint64_t)__double_as_longlong(__ldg(v + i));
-      const int ex = (int)((b >> 52) & 0x7FF);
-      if (ex != 0) e = max(e, ex - 1022);  // |x| < 2^{ex - 1023 + 1}
+    for (int q = 0; q < 2 * EW_PAIRS; ++q) {
+      const long long i = base + (long long)q * EW_THREADS + threadIdx.x;
+      b[q] = i < J.N ? (uint64_t)__double_as_longlong(__ldg(v + i)) : 0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < 2 * EW_PAIRS; ++q) {
+      emax[0] = max(emax[0], (int)((b[q] >> 52) & 0x7FF));  // subnormals and zeros: 0
     }
   }
-  warp_max_atomic(e, J.out_exp);
+  if (cur >= 0) block_exp_flush<1, 1022>(emax, jobs[cur].out_exp, red);
+}
+
+// grid for a grid-stride elementwise kernel: every SM filled with resident blocks, no more
+// blocks than virtual blocks
+template <typename K>
+unsigned ew_grid(K kernel, long long total) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, EW_THREADS, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return (unsigned)std::min<long long>(total, (long long)sms * per_sm);
 }
 
 InvFact make_invfact() {
@@ -287,12 +356,14 @@ InvFact make_invfact() {
 template <int P_>
 int launch_ew(int kind, const EJob* jobs, int njobs, long long blocks, const void* const* tab, cudaStream_t st) {
   if (kind == STEP_WEIGHTED) {
+    const unsigned grid = ew_grid(g_weighted_kernel<P_>, blocks);
     launch_begin(KC_WEIGHTED, st);
-    g_weighted_kernel<P_><<<(unsigned)blocks, EW_THREADS, 0, st>>>(jobs, njobs, tab);
+    g_weighted_kernel<P_><<<grid, EW_THREADS, 0, st>>>(jobs, njobs, blocks, tab);
   } else {
     static const InvFact inv = make_invfact();
+    const unsigned grid = ew_grid(g_squaring_kernel<P_>, blocks);
     launch_begin(KC_SQUARING, st);
-    g_squaring_kernel<P_><<<(unsigned)blocks, EW_THREADS, 0, st>>>(jobs, njobs, tab, inv);
+    g_squaring_kernel<P_><<<grid, EW_THREADS, 0, st>>>(jobs, njobs, blocks, tab, inv);
   }
   launch_end(st);
   PK_CHECK_LAUNCH();
@@ -887,7 +958,8 @@ int seq_launch_all(Seq& S, cudaStream_t st) {
       PK_RET(tc::mode_pass(P, s.shape, S.dStatus, st));
     } else if (s.kind == STEP_EXPSCAN) {
       launch_begin(KC_CONVERT, st);
-      g_expscan_kernel<<<(unsigned)s.total, EW_THREADS, 0, st>>>(S.dE + s.off, s.count, S.dPtrtab);
+      g_expscan_kernel<<<ew_grid(g_expscan_kernel, s.total), EW_THREADS, 0, st>>>(S.dE + s.off, s.count, s.total,
+                                                                                  S.dPtrtab);
       launch_end(st);
       PK_CHECK_LAUNCH();
     } else {
