@@ -122,8 +122,8 @@ __device__ __forceinline__ void mma_bf16_lo(uint32_t tmem_d, uint32_t a_lo, uint
 // tile's first chunk, where each accumulator's first MMA overwrites it -- the first touch of
 // accumulator a is pair (1, a + 1) at K-step 0.  E_IS_A puts E in the A operand (M = output
 // rows) and the input slices in B; otherwise the input slices are A.  XSLICE: bytes between
-// input slices.
-template <int KS, bool FIRST, bool E_IS_A, int ACC_COLS, int XSLICE>
+// input slices.  MASK: the accumulators this call issues for (bit a = accumulator a).
+template <int KS, bool FIRST, bool E_IS_A, int ACC_COLS, int XSLICE, int MASK = 15>
 __device__ __forceinline__ void issue_chunk(uint32_t acc0, uint32_t xlo, uint32_t elo, uint32_t idesc) {
 #pragma unroll
   for (int s = 1; s <= KS; ++s) {
@@ -132,6 +132,7 @@ __device__ __forceinline__ void issue_chunk(uint32_t acc0, uint32_t xlo, uint32_
       if (s + t > KS + 1) continue;
       const int L = s + t - 2;
       const int a = L < 3 ? L : 3;
+      if (!((MASK >> a) & 1)) continue;  // accumulator issued by the other MMA thread
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
         const uint32_t xd = xlo + (uint32_t)((((t - 1) * XSLICE) + ks * KSTEP_BYTES) >> 4);
@@ -649,25 +650,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
 }
 
 // ---------------------------------------------------------------- warp-specialised variant
-// Roles (14 warps = 448 threads, 128 registers a thread; 32-wide K chunks):
+// Roles of the warp-specialised kernel (15 warps = 480 threads; 32-wide K chunks):
 //   warps 0-7   producers: cut the operand digits of each chunk into the 2-stage ring;
 //               producer thread 0 also starts the chunk's E bulk copy
 //   warps 8-11  epilogue: drain the four TMEM accumulators (warp 8+q owns TMEM lanes 32q..32q+31,
 //               all columns), float-float, scale, store, exponent of the output
-//   warp 12     lane 0 issues the tcgen05 MMAs
+//   warps 12,14 lane 0 issues the tcgen05 MMAs of accumulators {0, 3} (warp 12) and {1, 2}
+//               (warp 14)
 //   warp 13     lane 0 resolves each tile's context (job lookup, input exponent, pointers) into a
 //               4-slot shared-memory ring ahead of the other roles, so that no role waits on a
 //               chain of dependent global loads at a tile boundary
-// mbarriers: full_x[2] (256 producer arrivals), full_e[2] (bulk-copy bytes), empty[2] (MMA
-// commit), tmem_full (MMA commit after a tile), tmem_empty (128 epilogue arrivals), done (final
-// MMA commit), slot_full[4] (scheduler), slot_empty[4] (every reader: 256 + 1 + 128).  The
-// producers fill the ring for the next tile while the epilogue drains the current one.  Every
-// wait is bounded; an expired wait sets a shared abort flag and the status word, every role
-// stops at its next check, the epilogue decides by a vote so that its named barrier stays
-// matched, and TMEM is freed only after the MMA thread saw its own MMAs complete.
+// (The double-buffered variant further below keeps one MMA thread: 14 warps = 448 threads.)
+// mbarriers: full_x[2] (256 producer arrivals), full_e[2] (bulk-copy bytes), empty[2] (one
+// MMA commit per issuing thread), tmem_full (likewise, after a tile), tmem_empty (128 epilogue
+// arrivals), done (final commit of each issuing thread), slot_full[4] (scheduler),
+// slot_empty[4] (every reader: 256 + 2 + 128).  The producers fill the ring for the next tile
+// while the epilogue drains the current one.  Every wait is bounded; an expired wait sets a
+// shared abort flag and the status word, every role stops at its next check, the epilogue
+// decides by a vote so that its named barrier stays matched, and TMEM is freed only after
+// both MMA threads saw their own MMAs complete.
 constexpr int WS_EPI0 = 8, WS_MMA = 12, WS_SCHED = 13, WS_THREADS = 448;
 constexpr int WS_PROD = 256, WS_EPI = 128, WS_SLOTS = 4;
 constexpr int WS_SLOT_READERS = WS_PROD + 1 + WS_EPI;
+// The warp-specialised kernel issues its MMAs from two threads (warps 12 and 14, on different
+// warp schedulers), each owning two of the four accumulators: one issuing thread that shares
+// its scheduler with two digit-cutting warps gets a tcgen05.mma out only every ~100 cycles,
+// while the tensor pipe retires one 128 x 128 x 16 MMA every 64.
+constexpr int WS_MMA2 = 14, WS_ISSUERS = 2, WS2_THREADS = 480;
+constexpr int WS2_SLOT_READERS = WS_PROD + WS_ISSUERS + WS_EPI;
+constexpr int WS_MASK1 = 0b1001, WS_MASK2 = 0b0110;  // accumulators {0, 3} and {1, 2}
 
 struct WsSlot {
   const void* in;
@@ -772,7 +783,7 @@ __device__ __forceinline__ void ff_combine(float d2, float d3, float d4, float d
 }
 
 template <int KS, bool IN_F64, bool TRANS>
-__global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
+__global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int HALF_BYTES = KS * SLICE_BYTES;
   constexpr int STAGE_BYTES = 2 * HALF_BYTES;
@@ -797,14 +808,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
     for (int q = 0; q < 2; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_x[q])), "r"(WS_PROD));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_e[q])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[q])), "r"(WS_ISSUERS));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(tmem_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tmem_full)), "r"(WS_ISSUERS));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tmem_empty)), "r"(WS_EPI));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done)), "r"(WS_ISSUERS));
     for (int q = 0; q < WS_SLOTS; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_full[q])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&slot_empty[q])), "r"(WS_SLOT_READERS));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&slot_empty[q])), "r"(WS2_SLOT_READERS));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_s = 0;
@@ -1008,9 +1019,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       const int emax = (int)(mx >> 23);
       if (lane == 0 && S.out_exp && emax > 0) atomicMax(S.out_exp, emax - 126);
     }
-  } else if (warp == WS_MMA) {
+  } else if (warp == WS_MMA || warp == WS_MMA2) {
     if (lane == 0) {
-      // ---------------------------------------------------------- MMA issuer
+      // ---------------------------------------------------------- MMA issuers (two threads)
+      const bool second = warp == WS_MMA2;
       uint32_t it = 0, tc = 0;
       bool issued = false;
       for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++tc) {
@@ -1028,16 +1040,22 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
           if (*abort_s) { stop = true; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           // descriptors built once per chunk; the issue loop only adds compile-time offsets
-          // (start-address units of 16 bytes) to 32-bit low words, so the single issuing thread
-          // keeps up with the tensor pipe
+          // (start-address units of 16 bytes) to 32-bit low words
           const uint32_t xa = smem_u32(smem + st * STAGE_BYTES);
           const uint32_t xlo = desc_lo(xa), elo = desc_lo(xa + HALF_BYTES);
-          if (c == 0)
-            issue_chunk<KS, true, !TRANS, 128, SLICE_BYTES>(tmem, xlo, elo, idesc);
-          else
-            issue_chunk<KS, false, !TRANS, 128, SLICE_BYTES>(tmem, xlo, elo, idesc);
+          if (second) {
+            if (c == 0)
+              issue_chunk<KS, true, !TRANS, 128, SLICE_BYTES, WS_MASK2>(tmem, xlo, elo, idesc);
+            else
+              issue_chunk<KS, false, !TRANS, 128, SLICE_BYTES, WS_MASK2>(tmem, xlo, elo, idesc);
+          } else {
+            if (c == 0)
+              issue_chunk<KS, true, !TRANS, 128, SLICE_BYTES, WS_MASK1>(tmem, xlo, elo, idesc);
+            else
+              issue_chunk<KS, false, !TRANS, 128, SLICE_BYTES, WS_MASK1>(tmem, xlo, elo, idesc);
+          }
           issued = true;
-          mma_commit(smem_u32(&empty[st]));
+          mma_commit(smem_u32(&empty[st]));  // arrives once this thread's MMAs of the chunk are done
         }
         if (stop) break;
         mma_commit(smem_u32(tmem_full));
@@ -1465,12 +1483,12 @@ size_t smem_bytes(int ks, int sub) {
 
 template <int KS, int SUB, bool IN_F64, bool TRANS>
 int launch_one(const GPass& P, int grid, bool ws, int* status, cudaStream_t st) {
-  // the warp-specialised kernel is built for 32-wide K chunks only (its 14 warps leave 128
+  // the warp-specialised kernel is built for 32-wide K chunks only (its 15 warps leave ~128
   // registers a thread, too few for the doubled raw-value buffers of 64-wide chunks)
   const bool use_ws = ws && SUB == 1;
   const size_t sm = use_ws ? ws_smem_bytes(KS) : smem_bytes(KS, SUB);
   auto kern = use_ws ? mode_kernel_ws<KS, IN_F64, TRANS> : mode_kernel<KS, SUB, IN_F64, TRANS>;
-  const int threads = use_ws ? WS_THREADS : NTHREADS;
+  const int threads = use_ws ? WS2_THREADS : NTHREADS;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) {
     set_error(std::string("tc mode kernel smem attribute: ") + cudaGetErrorString(e));
