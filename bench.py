@@ -133,7 +133,7 @@ def peaks():
 # DRAM traffic of the tensor-core mode kernel from the ncu capture summarised in
 # profiles/mode_kernel_ws_convdiff3d_n128_ncu_full.md (one launch of the z-mode node pass:
 # 11 vectors x N unknowns); valid only while the kernel source is the one captured.
-PROFILED_MODE_TRAFFIC = {"source_sha256_16": "5f383dad0f2a4c52", "bytes": 186.0928e6 + 128.35712e6,
+PROFILED_MODE_TRAFFIC = {"source_sha256_16": "bff4e504a7d05f08", "bytes": 186.136576e6 + 128.175616e6,
                          "vector_passes": 11, "N": 2097152}
 
 
