@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
 
 // ---------------------------------------------------------------- warp-specialised variant
 // Roles of the warp-specialised kernel (15 warps = 480 threads; 32-wide K chunks):
-//   warps 0-7   producers: cut the operand digits of each chunk into the 2-stage ring;
+//   warps 0-7   producers: cut the operand digits of each chunk into the stage ring;
 //               producer thread 0 also starts the chunk's E bulk copy
 //   warps 8-11  epilogue: drain the four TMEM accumulators (warp 8+q owns TMEM lanes 32q..32q+31,
 //               all columns), float-float, scale, store, exponent of the output
@@ -661,8 +661,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
 //               4-slot shared-memory ring ahead of the other roles, so that no role waits on a
 //               chain of dependent global loads at a tile boundary
 // (The double-buffered variant further below keeps one MMA thread: 14 warps = 448 threads.)
-// mbarriers: full_x[2] (256 producer arrivals), full_e[2] (bulk-copy bytes), empty[2] (one
-// MMA commit per issuing thread), tmem_full (likewise, after a tile), tmem_empty (128 epilogue
+// mbarriers: full_x[NST] (256 producer arrivals), full_e[NST] (bulk-copy bytes), empty[NST]
+// (one MMA commit per issuing thread), tmem_full (likewise, after a tile), tmem_empty (128 epilogue
 // arrivals), done (final commit of each issuing thread), slot_full[4] (scheduler),
 // slot_empty[4] (every reader: 256 + 2 + 128).  The producers fill the ring for the next tile
 // while the epilogue drains the current one.  Every wait is bounded; an expired wait sets a
@@ -692,12 +692,19 @@ struct WsSlot {
   int n, nsub, rb, eX, nrows_e, out_f64;
 };
 
-// shared-memory layout after the two stages
+// shared-memory layout after the stages
 constexpr int WS_BAR_BYTES = 256, WS_SCALE_BYTES = 512, WS_SLOT_BYTES = 512;
 static_assert(sizeof(WsSlot) * WS_SLOTS <= WS_SLOT_BYTES, "slot ring");
 
+// Stages of the warp-specialised kernel's operand ring (X and E slices of one 32-wide chunk
+// each): three up to 4 digit slices (3 x 64 KB), two above.  With two stages the producers
+// can cut chunk c + 2 only after the MMAs of chunk c completed, and the tensor pipe waited
+// for them on every tile's third and fourth chunk.
+__host__ __device__ constexpr int ws_stages(int ks) { return ks <= 4 ? 3 : 2; }
+static_assert(3 * 3 + 3 + 2 * WS_SLOTS <= WS_BAR_BYTES / 8, "mbarrier area");
+
 size_t ws_smem_bytes(int ks) {
-  return (size_t)2 * 2 * ks * SLICE_BYTES + WS_BAR_BYTES + WS_SCALE_BYTES + WS_SLOT_BYTES + 32;
+  return (size_t)ws_stages(ks) * 2 * ks * SLICE_BYTES + WS_BAR_BYTES + WS_SCALE_BYTES + WS_SLOT_BYTES + 32;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
@@ -787,16 +794,17 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int HALF_BYTES = KS * SLICE_BYTES;
   constexpr int STAGE_BYTES = 2 * HALF_BYTES;
-  uint8_t* tail = smem + 2 * STAGE_BYTES;
+  constexpr int NST = ws_stages(KS);
+  uint8_t* tail = smem + NST * STAGE_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
-  uint64_t* full_x = bars;        // [2]
-  uint64_t* full_e = bars + 2;    // [2]
-  uint64_t* empty = bars + 4;     // [2]
-  uint64_t* tmem_full = bars + 6;
-  uint64_t* tmem_empty = bars + 7;
-  uint64_t* done = bars + 8;
-  uint64_t* slot_full = bars + 9;    // [WS_SLOTS]
-  uint64_t* slot_empty = bars + 13;  // [WS_SLOTS]
+  uint64_t* full_x = bars;              // [NST]
+  uint64_t* full_e = bars + NST;        // [NST]
+  uint64_t* empty = bars + 2 * NST;     // [NST]
+  uint64_t* tmem_full = bars + 3 * NST;
+  uint64_t* tmem_empty = bars + 3 * NST + 1;
+  uint64_t* done = bars + 3 * NST + 2;
+  uint64_t* slot_full = bars + 3 * NST + 3;            // [WS_SLOTS]
+  uint64_t* slot_empty = bars + 3 * NST + 3 + WS_SLOTS;  // [WS_SLOTS]
   float* scale_s = reinterpret_cast<float*>(tail + WS_BAR_BYTES);  // 128 floats
   WsSlot* slots = reinterpret_cast<WsSlot*>(tail + WS_BAR_BYTES + WS_SCALE_BYTES);
   uint32_t* tmem_s = reinterpret_cast<uint32_t*>(tail + WS_BAR_BYTES + WS_SCALE_BYTES + WS_SLOT_BYTES);
@@ -805,7 +813,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long total_tiles = P.total_tiles;
   if (tid == 0) {
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < NST; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_x[q])), "r"(WS_PROD));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_e[q])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[q])), "r"(WS_ISSUERS));
@@ -856,7 +864,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
       const bool has_next = tile + gridDim.x < total_tiles;
       bool stop = false;
       for (int c = 0; c < nchunks; ++c, ++it) {
-        const uint32_t st = it & 1u, use = it >> 1;
+        const uint32_t st = it % NST, use = it / NST;
         uint8_t* sX = smem + st * STAGE_BYTES;
         uint8_t* sE = sX + HALF_BYTES;
         // the next chunk's raw values go in flight before the wait for a free stage, so that
@@ -917,8 +925,8 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
     }
     if (tid == 0 && *abort_s) {
       // bulk copies still in flight must land before the CTA's shared memory is released
-      for (int k = e_last; k >= 0 && k >= e_last - 1; --k)
-        mbar_wait(smem_u32(&full_e[k & 1]), ((uint32_t)k >> 1) & 1u);
+      for (int k = e_last; k >= 0 && k >= e_last - (NST - 1); --k)
+        mbar_wait(smem_u32(&full_e[k % NST]), ((uint32_t)k / NST) & 1u);
     }
   } else if (warp < WS_MMA) {
     // ------------------------------------------------------------ epilogue
@@ -1034,7 +1042,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
         const uint32_t idesc = TRANS ? make_idesc(128, S.nrows_e) : make_idesc(128, 128);
         bool stop = false;
         for (int c = 0; c < S.nsub; ++c, ++it) {
-          const uint32_t st = it & 1u, use = it >> 1;
+          const uint32_t st = it % NST, use = it / NST;
           if (!mbar_wait(smem_u32(&full_x[st]), use & 1u) || !mbar_wait(smem_u32(&full_e[st]), use & 1u))
             ws_fail(abort_s, status);
           if (*abort_s) { stop = true; break; }
