@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
 //   warp 13     lane 0 resolves each tile's context (job lookup, input exponent, pointers) into a
 //               4-slot shared-memory ring ahead of the other roles, so that no role waits on a
 //               chain of dependent global loads at a tile boundary
-// (The double-buffered variant further below keeps one MMA thread: 14 warps = 448 threads.)
+// The double-buffered variant further below uses the same roles.
 // mbarriers: full_x[NST] (256 producer arrivals), full_e[NST] (bulk-copy bytes), empty[NST]
 // (one MMA commit per issuing thread), tmem_full (likewise, after a tile), tmem_empty (128 epilogue
 // arrivals), done (final commit of each issuing thread), slot_full[4] (scheduler),
@@ -669,15 +669,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
 // shared abort flag and the status word, every role stops at its next check, the epilogue
 // decides by a vote so that its named barrier stays matched, and TMEM is freed only after
 // both MMA threads saw their own MMAs complete.
-constexpr int WS_EPI0 = 8, WS_MMA = 12, WS_SCHED = 13, WS_THREADS = 448;
+constexpr int WS_EPI0 = 8, WS_MMA = 12, WS_SCHED = 13;
 constexpr int WS_PROD = 256, WS_EPI = 128, WS_SLOTS = 4;
-constexpr int WS_SLOT_READERS = WS_PROD + 1 + WS_EPI;
 // The warp-specialised kernel issues its MMAs from two threads (warps 12 and 14, on different
 // warp schedulers), each owning two of the four accumulators: one issuing thread that shares
 // its scheduler with two digit-cutting warps gets a tcgen05.mma out only every ~100 cycles,
 // while the tensor pipe retires one 128 x 128 x 16 MMA every 64.
-constexpr int WS_MMA2 = 14, WS_ISSUERS = 2, WS2_THREADS = 480;
-constexpr int WS2_SLOT_READERS = WS_PROD + WS_ISSUERS + WS_EPI;
+constexpr int WS_MMA2 = 14, WS_ISSUERS = 2, WS_THREADS = 480;
+constexpr int WS_SLOT_READERS = WS_PROD + WS_ISSUERS + WS_EPI;
 constexpr int WS_MASK1 = 0b1001, WS_MASK2 = 0b0110;  // accumulators {0, 3} and {1, 2}
 
 struct WsSlot {
@@ -790,7 +789,7 @@ __device__ __forceinline__ void ff_combine(float d2, float d3, float d4, float d
 }
 
 template <int KS, bool IN_F64, bool TRANS>
-__global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
+__global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int HALF_BYTES = KS * SLICE_BYTES;
   constexpr int STAGE_BYTES = 2 * HALF_BYTES;
@@ -823,7 +822,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done)), "r"(WS_ISSUERS));
     for (int q = 0; q < WS_SLOTS; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_full[q])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&slot_empty[q])), "r"(WS2_SLOT_READERS));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&slot_empty[q])), "r"(WS_SLOT_READERS));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_s = 0;
@@ -943,7 +942,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
       // the vote is also the barrier after the scale writes; every epilogue thread decides alike
       if (epi_vote_any(!ok || *abort_s)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t mx = 0;   // largest |hi| bit pattern stored
+      float mxf = 0.0f;  // largest |hi| stored (one FMNMX per element)
       if (TRANS) {
         // TMEM lane = fiber r, column = output row i of this row block; stores coalesce over lanes
         const long long g = S.g0 + et;
@@ -966,7 +965,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
               ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
               const float sc = scale_s[cc + j];
               dst[(long long)j * S.R] = make_float2(hi * sc, lo * sc);
-              mx = max(mx, __float_as_uint(hi * sc) & 0x7FFFFFFFu);
+              mxf = fmaxf(mxf, fabsf(hi * sc));
             }
           } else if (vg) {
             double* dst = reinterpret_cast<double*>(S.out) + o0 + (long long)cc * S.R;
@@ -976,7 +975,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
               ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
               const float sc = scale_s[cc + j];
               dst[(long long)j * S.R] = ff_to_f64(hi * sc, lo * sc);
-              mx = max(mx, __float_as_uint(hi * sc) & 0x7FFFFFFFu);
+              mxf = fmaxf(mxf, fabsf(hi * sc));
             }
           }
         }
@@ -1002,7 +1001,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
               ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
               if (j < jn) {
                 dst[(long long)j * S.n] = make_float2(hi * sc, lo * sc);
-                mx = max(mx, __float_as_uint(hi * sc) & 0x7FFFFFFFu);
+                mxf = fmaxf(mxf, fabsf(hi * sc));
               }
             }
           } else if (vi) {
@@ -1013,7 +1012,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
               ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
               if (j < jn) {
                 dst[(long long)j * S.n] = ff_to_f64(hi * sc, lo * sc);
-                mx = max(mx, __float_as_uint(hi * sc) & 0x7FFFFFFFu);
+                mxf = fmaxf(mxf, fabsf(hi * sc));
               }
             }
           }
@@ -1021,6 +1020,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(tmem_empty));
+      uint32_t mx = __float_as_uint(mxf);  // non-negative: bit patterns order like the values
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       // |v| < 2^{biased - 126}; a zero vector keeps the slot's initial (very negative) value
@@ -1125,7 +1125,7 @@ __global__ void __launch_bounds__(WS2_THREADS, 1) mode_kernel_ws(const __grid_co
 // slices as B (N = 64) in both orientations, so that one tile's four level accumulators take
 // 4 x 64 TMEM columns and two tiles alternate between columns [0, 256) and [256, 512): the
 // epilogue drains tile t while the MMAs of tile t+1 run.  Same roles as the warp-specialised
-// kernel (8 producer, 4 epilogue, 1 MMA, 1 scheduler warp).  Producers hold three chunks
+// kernel (8 producer, 4 epilogue, 2 MMA-issuing, 1 scheduler warp).  Producers hold three chunks
 // (8 values a thread each) in registers, so the loads of chunk c+2 are in flight while chunk c
 // is cut.  With fibers on the TMEM columns, a transposed pass's outputs (fiber = fastest
 // index) are staged in shared memory and written back row by row, coalesced.  Every job of a
@@ -1134,8 +1134,12 @@ constexpr int DB_XSLICE = 64 * KC * 2;       // one slice of a 64-fiber chunk: 4
 constexpr int DB_STAGE_PITCH = 528;          // bytes per staged output row (64 x 8 B + 16)
 constexpr int DB_STAGE_BYTES = 128 * DB_STAGE_PITCH;
 
+// stages of the double-buffered kernel's operand ring: three up to 4 digit slices, two above
+__host__ __device__ constexpr int db_stages(int ks) { return ks <= 4 ? 3 : 2; }
+static_assert(3 * 3 + 5 + 2 * WS_SLOTS <= WS_BAR_BYTES / 8, "mbarrier area (double-buffered kernel)");
+
 size_t db_smem_bytes(int ks) {
-  return (size_t)2 * ks * (DB_XSLICE + SLICE_BYTES) + DB_STAGE_BYTES + WS_BAR_BYTES + WS_SLOT_BYTES + 32;
+  return (size_t)db_stages(ks) * ks * (DB_XSLICE + SLICE_BYTES) + DB_STAGE_BYTES + WS_BAR_BYTES + WS_SLOT_BYTES + 32;
 }
 
 // 8 consecutive values (k = kc .. kc+7) of fiber g0 + fib
@@ -1173,17 +1177,18 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int XBYTES = KS * DB_XSLICE;
   constexpr int STAGE = XBYTES + KS * SLICE_BYTES;
-  uint8_t* staging = smem + 2 * STAGE;
+  constexpr int NST = db_stages(KS);
+  uint8_t* staging = smem + NST * STAGE;
   uint8_t* tail = staging + DB_STAGE_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
-  uint64_t* full_x = bars;          // [2]
-  uint64_t* full_e = bars + 2;      // [2]
-  uint64_t* empty = bars + 4;       // [2]
-  uint64_t* tmem_full = bars + 6;   // [2] one per TMEM buffer
-  uint64_t* tmem_empty = bars + 8;  // [2]
-  uint64_t* done = bars + 10;
-  uint64_t* slot_full = bars + 11;  // [WS_SLOTS]
-  uint64_t* slot_empty = bars + 15; // [WS_SLOTS]
+  uint64_t* full_x = bars;                  // [NST]
+  uint64_t* full_e = bars + NST;            // [NST]
+  uint64_t* empty = bars + 2 * NST;         // [NST]
+  uint64_t* tmem_full = bars + 3 * NST;     // [2] one per TMEM buffer
+  uint64_t* tmem_empty = bars + 3 * NST + 2;  // [2]
+  uint64_t* done = bars + 3 * NST + 4;
+  uint64_t* slot_full = bars + 3 * NST + 5;             // [WS_SLOTS]
+  uint64_t* slot_empty = bars + 3 * NST + 5 + WS_SLOTS; // [WS_SLOTS]
   WsSlot* slots = reinterpret_cast<WsSlot*>(tail + WS_BAR_BYTES);
   uint32_t* tmem_s = reinterpret_cast<uint32_t*>(tail + WS_BAR_BYTES + WS_SLOT_BYTES);
   volatile int* abort_s = reinterpret_cast<volatile int*>(tail + WS_BAR_BYTES + WS_SLOT_BYTES + 16);
@@ -1191,14 +1196,16 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long total_tiles = P.total_tiles;
   if (tid == 0) {
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < NST; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_x[q])), "r"(WS_PROD));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_e[q])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tmem_full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[q])), "r"(WS_ISSUERS));
+    }
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tmem_full[q])), "r"(WS_ISSUERS));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tmem_empty[q])), "r"(WS_EPI));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done)), "r"(WS_ISSUERS));
     for (int q = 0; q < WS_SLOTS; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_full[q])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&slot_empty[q])), "r"(WS_SLOT_READERS));
@@ -1242,7 +1249,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       const bool has_next = tile + gridDim.x < total_tiles;
       bool have_next = false;
       for (int c = 0; c < nchunks; ++c, ++it) {
-        const uint32_t st = it & 1u, use = it >> 1;
+        const uint32_t st = it % NST, use = it / NST;
         uint8_t* sX = smem + st * STAGE;
         uint8_t* sE = sX + XBYTES;
         // chunk it + 2 in flight before the wait for a free stage
@@ -1296,8 +1303,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
     }
     if (tid == 0 && *abort_s) {
       // bulk copies still in flight must land before the CTA's shared memory is released
-      for (int k = e_last; k >= 0 && k >= e_last - 1; --k)
-        mbar_wait(smem_u32(&full_e[k & 1]), ((uint32_t)k >> 1) & 1u);
+      for (int k = e_last; k >= 0 && k >= e_last - (NST - 1); --k)
+        mbar_wait(smem_u32(&full_e[k % NST]), ((uint32_t)k / NST) & 1u);
     }
   } else if (warp < WS_MMA) {
     // ------------------------------------------------------------ epilogue
@@ -1394,9 +1401,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       const int emax = (int)(mx >> 23);
       if (lane == 0 && S.out_exp && emax > 0) atomicMax(S.out_exp, emax - 126);
     }
-  } else if (warp == WS_MMA) {
+  } else if (warp == WS_MMA || warp == WS_MMA2) {
     if (lane == 0) {
-      // ---------------------------------------------------------- MMA issuer
+      // ---------------------------------------------------------- MMA issuers (two threads)
+      const bool second = warp == WS_MMA2;
       uint32_t it = 0, tc = 0;
       bool issued = false;
       const uint32_t idesc = make_idesc(128, 64);
@@ -1409,7 +1417,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         bool stop = false;
         for (int c = 0; c < S.nsub; ++c, ++it) {
-          const uint32_t st = it & 1u, use = it >> 1;
+          const uint32_t st = it % NST, use = it / NST;
           if (!mbar_wait(smem_u32(&full_x[st]), use & 1u) || !mbar_wait(smem_u32(&full_e[st]), use & 1u))
             ws_fail(abort_s, status);
           if (*abort_s) { stop = true; break; }
@@ -1417,10 +1425,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
           const uint32_t xa = smem_u32(smem + st * STAGE);
           const uint32_t xlo = desc_lo(xa), elo = desc_lo(xa + XBYTES);
           const uint32_t acc0 = tmem + 256u * b;
-          if (c == 0)
-            issue_chunk<KS, true, true, 64, DB_XSLICE>(acc0, xlo, elo, idesc);
-          else
-            issue_chunk<KS, false, true, 64, DB_XSLICE>(acc0, xlo, elo, idesc);
+          if (second) {
+            if (c == 0)
+              issue_chunk<KS, true, true, 64, DB_XSLICE, WS_MASK2>(acc0, xlo, elo, idesc);
+            else
+              issue_chunk<KS, false, true, 64, DB_XSLICE, WS_MASK2>(acc0, xlo, elo, idesc);
+          } else {
+            if (c == 0)
+              issue_chunk<KS, true, true, 64, DB_XSLICE, WS_MASK1>(acc0, xlo, elo, idesc);
+            else
+              issue_chunk<KS, false, true, 64, DB_XSLICE, WS_MASK1>(acc0, xlo, elo, idesc);
+          }
           issued = true;
           mma_commit(smem_u32(&empty[st]));
         }
@@ -1496,7 +1511,7 @@ int launch_one(const GPass& P, int grid, bool ws, int* status, cudaStream_t st) 
   const bool use_ws = ws && SUB == 1;
   const size_t sm = use_ws ? ws_smem_bytes(KS) : smem_bytes(KS, SUB);
   auto kern = use_ws ? mode_kernel_ws<KS, IN_F64, TRANS> : mode_kernel<KS, SUB, IN_F64, TRANS>;
-  const int threads = use_ws ? WS2_THREADS : NTHREADS;
+  const int threads = use_ws ? WS_THREADS : NTHREADS;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) {
     set_error(std::string("tc mode kernel smem attribute: ") + cudaGetErrorString(e));

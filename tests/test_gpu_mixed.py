@@ -52,6 +52,23 @@ def test_convdiff3d_mixed_vs_fp64_path(slices):
         assert P.rel_err_2(om[l], of[l]) <= BOUND[slices], (slices, l, P.rel_err_2(om[l], of[l]))
 
 
+@pytest.mark.parametrize("kernel", ["ws", "db", "classic"])
+@pytest.mark.parametrize("slices", [3, 4, 5])
+def test_mode_kernel_variants_vs_fp64_path(kernel, slices, monkeypatch):
+    """Every mode-kernel variant (warp-specialised default, double-buffered, single-role) at
+    2- and 3-stage operand rings (up to 4 slices: three stages) and several tiles per CTA:
+    n >= 64 on every axis so that the double-buffered kernel is eligible; 160 = 128 + 32 puts a
+    second E row block and a ragged tail on one axis."""
+    if kernel != "ws":
+        monkeypatch.setenv("PHIKRON_MODE_KERNEL", kernel)
+    shape = (64, 160, 96)
+    fac = [W.convdiff_factor(n) for n in shape]
+    v = W.uniform_vector(shape, 9)
+    om, of, info = _mixed_and_fp64(fac, 1e-2, 3, 1e-10, v, slices)
+    for l in range(4):
+        assert P.rel_err_2(om[l], of[l]) <= BOUND[slices], (kernel, slices, l, P.rel_err_2(om[l], of[l]))
+
+
 def test_convdiff3d_mixed_vs_exact_definition():
     shape = (16, 32, 48)
     fac = [W.convdiff_factor(n) for n in shape]
