@@ -165,6 +165,24 @@ int phikron_apply_combo(phikron_plan_t plan, const double* B, double* Out, void*
  */
 int phikron_apply_host(phikron_plan_t plan, const double* V_host, double* Out_host, void* stream);
 
+/*
+ * phikron_apply_host_many -- phikron_apply_host over `count` vectors with the transfers
+ * pipelined: while vector j is applied, vector j+1 is copied in and the results of vector
+ * j-1 are copied out (one copy stream per direction), so that in steady state a vector costs
+ * max(apply, copy-in, copy-out) instead of their sum.
+ *   V_host   : HOST, count x N float64, vector j at V_host + j*N.
+ *   Out_host : HOST, count x (l_max+1) x N float64 (x2 with half_step), vector j's results at
+ *              Out_host + j*(l_max+1)*N (same layout as phikron_apply's Out).
+ *   count    : >= 1, else EINVAL (as for NULL pointers).
+ * Host buffers must be pinned (cudaHostAlloc / cudaHostRegister) for the copies to overlap
+ * the applies; pageable buffers give correct results with serialised copies.  The first call
+ * on a plan allocates a second device staging set (N + (l_max+1)*N float64, x2 outputs with
+ * half_step) and creates two copy streams and seven events, all freed by phikron_destroy;
+ * later calls allocate nothing.  Synchronous: returns when every result is in Out_host.
+ * Results are bitwise those of phikron_apply on each vector.
+ */
+int phikron_apply_host_many(phikron_plan_t plan, const double* V_host, double* Out_host, int count, void* stream);
+
 typedef struct phikron_info {
   int    dims, n[PHIKRON_MAX_DIMS];
   int64_t N;

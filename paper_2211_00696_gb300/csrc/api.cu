@@ -71,6 +71,10 @@ double norm_one(const double* a, int n) {
 }  // namespace
 
 Plan::~Plan() {
+  for (cudaEvent_t e : {ev_in[0], ev_in[1], ev_comp[0], ev_comp[1], ev_out[0], ev_out[1], ev_start})
+    if (e) cudaEventDestroy(e);
+  if (cp_in) cudaStreamDestroy(cp_in);
+  if (cp_out) cudaStreamDestroy(cp_out);
   for (void* p : allocations) cudaFree(p);
   if (mixed && mixed_free) mixed_free(mixed);
 }
@@ -692,6 +696,63 @@ int phikron_apply_combo(phikron_plan_t plan, const double* B, double* Out, void*
   if (dg.rc != PHIKRON_OK) return dg.rc;
   ProfScope ps(&P.prof);
   return apply_combo_f64(P, B, Out, static_cast<cudaStream_t>(stream));
+}
+
+// Pipelined host-buffer applies: vector j is applied on `stream` from staging buffer j % 2
+// while vector j + 1 is copied in on one copy stream and the results of vector j - 1 are
+// copied out on another, so that both link directions and the GPU are busy at once.
+// Events order each reuse of a staging buffer after the work that last touched it.
+int phikron_apply_host_many(phikron_plan_t plan, const double* V_host, double* Out_host, int count, void* stream) {
+  clear_error();
+  if (!plan || !V_host || !Out_host || count < 1) {
+    set_error("phikron_apply_host_many: NULL argument or count < 1");
+    return PHIKRON_EINVAL;
+  }
+  Plan& P = plan->impl;
+  DeviceGuard dg(P.opts.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t in_elems = (size_t)P.N;
+  const size_t out_elems = (size_t)P.N * (P.p + 1) * (P.opts.half_step ? 2 : 1);
+  if (!P.dV2) {
+    PK_RET(P.alloc((void**)&P.dV2, sizeof(double) * in_elems));
+    PK_RET(P.alloc((void**)&P.dOut2, sizeof(double) * out_elems));
+    PK_TRY_CUDA(cudaStreamCreateWithFlags(&P.cp_in, cudaStreamNonBlocking));
+    PK_TRY_CUDA(cudaStreamCreateWithFlags(&P.cp_out, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&P.ev_in[0], &P.ev_in[1], &P.ev_comp[0], &P.ev_comp[1], &P.ev_out[0], &P.ev_out[1], &P.ev_start})
+      PK_TRY_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
+  double* Vd[2] = {P.dV, P.dV2};
+  double* Od[2] = {P.dOut, P.dOut2};
+  // the copy streams start after whatever the caller queued on `stream` before this call
+  PK_TRY_CUDA(cudaEventRecord(P.ev_start, st));
+  PK_TRY_CUDA(cudaStreamWaitEvent(P.cp_in, P.ev_start, 0));
+  PK_TRY_CUDA(cudaStreamWaitEvent(P.cp_out, P.ev_start, 0));
+  for (int j = 0; j < count; ++j) {
+    const int b = j & 1;
+    // staging input b was last read by the apply of vector j - 2
+    if (j >= 2) PK_TRY_CUDA(cudaStreamWaitEvent(P.cp_in, P.ev_comp[b], 0));
+    PK_TRY_CUDA(cudaMemcpyAsync(Vd[b], V_host + (size_t)j * in_elems, sizeof(double) * in_elems,
+                                cudaMemcpyHostToDevice, P.cp_in));
+    PK_TRY_CUDA(cudaEventRecord(P.ev_in[b], P.cp_in));
+    // the apply needs its input, and staging output b must have been copied out (vector j - 2)
+    PK_TRY_CUDA(cudaStreamWaitEvent(st, P.ev_in[b], 0));
+    if (j >= 2) PK_TRY_CUDA(cudaStreamWaitEvent(st, P.ev_out[b], 0));
+    {
+      ProfScope ps(&P.prof);
+      PK_RET(apply_dispatch(P, 1, Vd[b], Od[b], st));
+    }
+    PK_TRY_CUDA(cudaEventRecord(P.ev_comp[b], st));
+    PK_TRY_CUDA(cudaStreamWaitEvent(P.cp_out, P.ev_comp[b], 0));
+    PK_TRY_CUDA(cudaMemcpyAsync(Out_host + (size_t)j * out_elems, Od[b], sizeof(double) * out_elems,
+                                cudaMemcpyDeviceToHost, P.cp_out));
+    PK_TRY_CUDA(cudaEventRecord(P.ev_out[b], P.cp_out));
+  }
+  // `stream` is ordered after the last copy-out, then everything is complete on return
+  PK_TRY_CUDA(cudaStreamWaitEvent(st, P.ev_out[(count - 1) & 1], 0));
+  PK_TRY_CUDA(cudaStreamSynchronize(st));
+  PK_TRY_CUDA(cudaStreamSynchronize(P.cp_in));
+  return PHIKRON_OK;
 }
 
 int phikron_apply_host(phikron_plan_t plan, const double* V_host, double* Out_host, void* stream) {

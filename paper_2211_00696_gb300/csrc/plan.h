@@ -55,6 +55,13 @@ struct Plan {
   double* dYn = nullptr;
   double* dV = nullptr;      // staging for phikron_apply_host
   double* dOut = nullptr;
+  // second staging set, copy streams and events of phikron_apply_host_many (created by its
+  // first call)
+  double* dV2 = nullptr;
+  double* dOut2 = nullptr;
+  cudaStream_t cp_in = nullptr, cp_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr;
 
   // mixed-precision state (owned by the precision back-end; see precision_setup)
   void* mixed = nullptr;

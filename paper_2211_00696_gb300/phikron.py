@@ -77,6 +77,7 @@ SIGNATURES = {
     "phikron_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "phikron_apply_many": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "phikron_apply_host": (C.c_int, [C.c_void_p, _DP, _DP, C.c_void_p]),
+    "phikron_apply_host_many": (C.c_int, [C.c_void_p, _DP, _DP, C.c_int, C.c_void_p]),
     "phikron_plan_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "phikron_plan_nodes": (C.c_int, [C.c_void_p, _DP, _DP]),
     "phikron_destroy": (None, [C.c_void_p]),
@@ -275,6 +276,23 @@ class Plan:
         st = 0 if stream is None else _stream_ptr(stream)
         _check(lib().phikron_apply_host(self._h, C.cast(C.c_void_p(v_ptr), _DP),
                                         C.cast(C.c_void_p(out_ptr), _DP), C.c_void_p(st)))
+
+    def apply_host_many(self, v: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """Host-memory applies of count vectors (v: (count, N)) with pipelined transfers;
+        returns (count, l_max+1, N).  Pinned buffers (apply_host_many_ptr) overlap the copies."""
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, self.N)
+        count = v.shape[0]
+        if out is None:
+            out = np.empty((count, self.nout, self.N))
+        st = 0 if stream is None else _stream_ptr(stream)
+        _check(lib().phikron_apply_host_many(self._h, _dp(v), _dp(out), count, C.c_void_p(st)))
+        return out
+
+    def apply_host_many_ptr(self, v_ptr: int, out_ptr: int, count: int, stream=None):
+        """apply_host_many on raw (e.g. pinned torch) host pointers."""
+        st = 0 if stream is None else _stream_ptr(stream)
+        _check(lib().phikron_apply_host_many(self._h, C.cast(C.c_void_p(v_ptr), _DP),
+                                             C.cast(C.c_void_p(out_ptr), _DP), count, C.c_void_p(st)))
 
     def check_status(self):
         """Raises PhikronError(ETIMEOUT) if a bounded device wait of an earlier apply expired."""

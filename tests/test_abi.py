@@ -88,6 +88,9 @@ def test_invalid_arguments_return_einval_without_gpu():
         pk.Plan([np.eye(3), np.full((3, 3), np.nan)], 0.1, 2, 1e-10)
     with pytest.raises(pk.PhikronError):
         pk.Plan([np.eye(3), np.eye(3)], 0.1, 2, 0.0)          # tol <= 0
+    # pipelined host applies: argument checks run before any device call
+    L = pk.lib()
+    assert L.phikron_apply_host_many(None, None, None, 1, None) == B.EINVAL
     # exponential integrators: argument checks run before any device call
     for bad in (dict(method=4), dict(method=1, tau=0.0), dict(method=2, nonlinearity=7)):
         kw = dict(tau=1e-2, nonlinearity=pk.NONLIN_ALLEN_CAHN)
