@@ -133,7 +133,7 @@ def peaks():
 # DRAM traffic of the tensor-core mode kernel from the ncu capture summarised in
 # profiles/mode_kernel_ws_convdiff3d_n128_ncu_full.md (one launch of the z-mode node pass:
 # 11 vectors x N unknowns); valid only while the kernel source is the one captured.
-PROFILED_MODE_TRAFFIC = {"source_sha256_16": "bff4e504a7d05f08", "bytes": 186.136576e6 + 128.175616e6,
+PROFILED_MODE_TRAFFIC = {"source_sha256_16": "dc42b2fa54354838", "bytes": 186.191872e6 + 128.318976e6,
                          "vector_passes": 11, "N": 2097152}
 
 
@@ -316,14 +316,14 @@ def run_allen_cahn(args):
     print(json.dumps(line), flush=True)
 
 
-def fp64_gpu_compare(prob, V, out_shape, flush, golden, dev, local, steps=3):
-    """The same workload on the float64 GPU path (float64 DFMA mode products), timed the same
-    way: the comparison the metric names (mixed vs FP64 GPU at the stated accuracy)."""
+def fp64_gpu_compare(prob, V, out_shape, flush, golden, dev, local, tol, steps=3):
+    """The same workload on the float64 GPU path (float64 DFMA mode products) at the mixed arm's
+    quadrature tolerance (the same (s, m)), timed the same way: the comparison the metric names
+    (mixed vs FP64 GPU at the stated accuracy)."""
     import torch
 
     import paper_2211_00696_gb300 as pk
-    plan = pk.Plan(prob.factors, prob.tau, prob.l_max, PRECISIONS["fp64"][1], precision=pk.PREC_FP64,
-                   device=local)
+    plan = pk.Plan(prob.factors, prob.tau, prob.l_max, tol, precision=pk.PREC_FP64, device=local)
     Out = torch.empty(out_shape, dtype=torch.float64, device=dev)
     plan.apply(V, Out)
     torch.cuda.synchronize()
@@ -341,7 +341,7 @@ def fp64_gpu_compare(prob, V, out_shape, flush, golden, dev, local, steps=3):
     info = plan.info()
     plan.close()
     ms = tot / steps
-    return {"value": prob.N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+    return {"value": prob.N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "tol": tol,
             "s": info["s"], "m": info["m"], "actions": info["actions"], "rel_err_sampled": errs}
 
 
@@ -484,7 +484,7 @@ def run_ours(args):
                     "single_call_api": "phikron_apply_host, one synchronous call per step"},
         }
         if args.fp64_compare and args.precision != "fp64":
-            line["fp64_gpu"] = fp64_gpu_compare(prob, V, Out.shape, flush, golden, dev, local)
+            line["fp64_gpu"] = fp64_gpu_compare(prob, V, Out.shape, flush, golden, dev, local, tol)
         if args.cpu_baseline and world == 1:
             from oracle import planner as PL
             s, m, _ = PL.setup_quadrature(tol, prob.l_max, PL.alpha_inf(prob.factors, prob.tau))
