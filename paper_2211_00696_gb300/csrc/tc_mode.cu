@@ -253,6 +253,33 @@ __device__ __forceinline__ void cut_ff_float(float hi, float lo, float sc, float
   }
 }
 
+// Packed FP32x2 arithmetic (one instruction for two lanes, each lane IEEE round-to-nearest
+// like the scalar FADD/FMUL): the digit cutting and the accumulator combination work on pairs
+// of independent elements, so the producer and epilogue warps issue about half the FP32
+// instructions.  a - b is one fused multiply-add, b * (-1) + a, rounded once like FSUB.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// cut_ff_float for two elements at once (lane x: element (hi.x, lo.x), lane y: (hi.y, lo.y));
+// bitwise the scalar results
+template <int KS>
+__device__ __forceinline__ void cut_ff_float2(float2 hi, float2 lo, float sc, float2* v) {
+  const float2 sc2 = make_float2(sc, sc);
+  float2 r = mul2(hi, sc2);
+  const float2 l = mul2(lo, sc2);
+  constexpr int FOLD = KS < 4 ? KS : 4;
+#pragma unroll
+  for (int t = 1; t <= KS; ++t) {
+    if (t == FOLD) r = add2(r, l);
+    const float Ms = __uint_as_float((uint32_t)(127 + 23 - 8 * t) << 23) * 1.5f;
+    const float2 M = make_float2(Ms, Ms);
+    const float2 q = sub2(add2(r, M), M);
+    v[t - 1] = q;
+    r = sub2(r, q);
+  }
+}
+
 // two FP32 values exactly representable in BF16 -> (bf16(b) << 16) | bf16(a)
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   uint32_t d;
@@ -500,11 +527,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
 #pragma unroll
             for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
           } else {
-            float v0[KS], v1[KS];
-            cut_ff_float<KS>(raw[q].f[e].x, raw[q].f[e].y, xsc, v0);
-            cut_ff_float<KS>(raw[q].f[e + 1].x, raw[q].f[e + 1].y, xsc, v1);
+            float2 v[KS];
+            cut_ff_float2<KS>(make_float2(raw[q].f[e].x, raw[q].f[e + 1].x), make_float2(raw[q].f[e].y, raw[q].f[e + 1].y), xsc, v);
 #pragma unroll
-            for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v0[sl], v1[sl]);
+            for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v[sl].x, v[sl].y);
           }
         }
         const uint32_t off = chunk_offset(orow, kq);
@@ -788,6 +814,31 @@ __device__ __forceinline__ void ff_combine(float d2, float d3, float d4, float d
   fast_two_sum(hi, lo, hi, lo);
 }
 
+// ff_combine for two columns at once (packed FP32x2; bitwise the scalar results)
+template <int KS>
+__device__ __forceinline__ void ff_combine2(float2 d2, float2 d3, float2 d4, float2 d5, float2& hi, float2& lo) {
+  float2 h, l;
+  if (KS <= 5) {
+    h = add2(d2, d3);
+    const float2 bb = sub2(h, d2);
+    const float2 eh = add2(sub2(d2, sub2(h, bb)), sub2(d3, bb));
+    l = add2(eh, add2(d4, d5));
+  } else {
+    const float2 t45 = add2(d4, d5);
+    const float2 b45 = sub2(t45, d4);
+    const float2 e45 = add2(sub2(d4, sub2(t45, b45)), sub2(d5, b45));
+    const float2 u = add2(d3, t45);
+    const float2 bu = sub2(u, d3);
+    const float2 eu = add2(sub2(d3, sub2(u, bu)), sub2(t45, bu));
+    h = add2(d2, u);
+    const float2 bh = sub2(h, d2);
+    const float2 eh = add2(sub2(d2, sub2(h, bh)), sub2(u, bh));
+    l = add2(eh, add2(eu, e45));
+  }
+  hi = add2(h, l);
+  lo = sub2(l, sub2(hi, h));
+}
+
 template <int KS, bool IN_F64, bool TRANS>
 __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -901,11 +952,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
 #pragma unroll
               for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
             } else {
-              float v0[KS], v1[KS];
-              cut_ff_float<KS>(raw[g2].f[e].x, raw[g2].f[e].y, xsc, v0);
-              cut_ff_float<KS>(raw[g2].f[e + 1].x, raw[g2].f[e + 1].y, xsc, v1);
+              float2 v[KS];
+              cut_ff_float2<KS>(make_float2(raw[g2].f[e].x, raw[g2].f[e + 1].x), make_float2(raw[g2].f[e].y, raw[g2].f[e + 1].y), xsc, v);
 #pragma unroll
-              for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v0[sl], v1[sl]);
+              for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v[sl].x, v[sl].y);
             }
           }
           const int g = 2 * kh + g2;
@@ -960,22 +1010,32 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
           if (vg && !S.out_f64) {
             float2* dst = reinterpret_cast<float2*>(S.out) + o0 + (long long)cc * S.R;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              float hi, lo;
-              ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
-              const float sc = scale_s[cc + j];
-              dst[(long long)j * S.R] = make_float2(hi * sc, lo * sc);
-              mxf = fmaxf(mxf, fabsf(hi * sc));
+            for (int j = 0; j < 16; j += 2) {
+              float2 hi, lo;
+              ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
+                              make_float2(d4[j], d4[j + 1]),
+                              KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
+              const float2 sc = *reinterpret_cast<const float2*>(scale_s + cc + j);
+              hi = mul2(hi, sc);
+              lo = mul2(lo, sc);
+              dst[(long long)j * S.R] = make_float2(hi.x, lo.x);
+              dst[(long long)(j + 1) * S.R] = make_float2(hi.y, lo.y);
+              mxf = fmaxf(mxf, fmaxf(fabsf(hi.x), fabsf(hi.y)));
             }
           } else if (vg) {
             double* dst = reinterpret_cast<double*>(S.out) + o0 + (long long)cc * S.R;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              float hi, lo;
-              ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
-              const float sc = scale_s[cc + j];
-              dst[(long long)j * S.R] = ff_to_f64(hi * sc, lo * sc);
-              mxf = fmaxf(mxf, fabsf(hi * sc));
+            for (int j = 0; j < 16; j += 2) {
+              float2 hi, lo;
+              ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
+                              make_float2(d4[j], d4[j + 1]),
+                              KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
+              const float2 sc = *reinterpret_cast<const float2*>(scale_s + cc + j);
+              hi = mul2(hi, sc);
+              lo = mul2(lo, sc);
+              dst[(long long)j * S.R] = ff_to_f64(hi.x, lo.x);
+              dst[(long long)(j + 1) * S.R] = ff_to_f64(hi.y, lo.y);
+              mxf = fmaxf(mxf, fmaxf(fabsf(hi.x), fabsf(hi.y)));
             }
           }
         }
@@ -996,23 +1056,39 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
           if (vi && !S.out_f64) {
             float2* dst = reinterpret_cast<float2*>(S.out) + o0 + (long long)cc * S.n;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              float hi, lo;
-              ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
+            for (int j = 0; j < 16; j += 2) {
+              float2 hi, lo;
+              ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
+                              make_float2(d4[j], d4[j + 1]),
+                              KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
+              hi = mul2(hi, make_float2(sc, sc));
+              lo = mul2(lo, make_float2(sc, sc));
               if (j < jn) {
-                dst[(long long)j * S.n] = make_float2(hi * sc, lo * sc);
-                mxf = fmaxf(mxf, fabsf(hi * sc));
+                dst[(long long)j * S.n] = make_float2(hi.x, lo.x);
+                mxf = fmaxf(mxf, fabsf(hi.x));
+              }
+              if (j + 1 < jn) {
+                dst[(long long)(j + 1) * S.n] = make_float2(hi.y, lo.y);
+                mxf = fmaxf(mxf, fabsf(hi.y));
               }
             }
           } else if (vi) {
             double* dst = reinterpret_cast<double*>(S.out) + o0 + (long long)cc * S.n;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              float hi, lo;
-              ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hi, lo);
+            for (int j = 0; j < 16; j += 2) {
+              float2 hi, lo;
+              ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
+                              make_float2(d4[j], d4[j + 1]),
+                              KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
+              hi = mul2(hi, make_float2(sc, sc));
+              lo = mul2(lo, make_float2(sc, sc));
               if (j < jn) {
-                dst[(long long)j * S.n] = ff_to_f64(hi * sc, lo * sc);
-                mxf = fmaxf(mxf, fabsf(hi * sc));
+                dst[(long long)j * S.n] = ff_to_f64(hi.x, lo.x);
+                mxf = fmaxf(mxf, fabsf(hi.x));
+              }
+              if (j + 1 < jn) {
+                dst[(long long)(j + 1) * S.n] = ff_to_f64(hi.y, lo.y);
+                mxf = fmaxf(mxf, fabsf(hi.y));
               }
             }
           }
@@ -1282,11 +1358,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
 #pragma unroll
             for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
           } else {
-            float v0[KS], v1[KS];
-            cut_ff_float<KS>(r0.f[e].x, r0.f[e].y, xsc, v0);
-            cut_ff_float<KS>(r0.f[e + 1].x, r0.f[e + 1].y, xsc, v1);
+            float2 v[KS];
+            cut_ff_float2<KS>(make_float2(r0.f[e].x, r0.f[e + 1].x), make_float2(r0.f[e].y, r0.f[e + 1].y), xsc, v);
 #pragma unroll
-            for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v0[sl], v1[sl]);
+            for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(v[sl].x, v[sl].y);
           }
         }
         const uint32_t off = chunk_offset(fib, kg);
@@ -1336,11 +1411,19 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
         tmem_wait_ld();
         float hs[16], ls[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          ff_combine<KS>(d2[j], d3[j], d4[j], KS >= 4 ? d5[j] : 0.0f, hs[j], ls[j]);
-          hs[j] *= sc;
-          ls[j] *= sc;
-          mx = max(mx, __float_as_uint(hs[j]) & 0x7FFFFFFFu);
+        for (int j = 0; j < 16; j += 2) {
+          float2 hi, lo;
+          ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
+                          make_float2(d4[j], d4[j + 1]),
+                          KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
+          hi = mul2(hi, make_float2(sc, sc));
+          lo = mul2(lo, make_float2(sc, sc));
+          hs[j] = hi.x;
+          hs[j + 1] = hi.y;
+          ls[j] = lo.x;
+          ls[j + 1] = lo.y;
+          mx = max(mx, __float_as_uint(hi.x) & 0x7FFFFFFFu);
+          mx = max(mx, __float_as_uint(hi.y) & 0x7FFFFFFFu);
         }
         if (TRANS) {
           // row i of the staged tile: 16 columns as 8 pairs of 16 bytes
