@@ -139,7 +139,7 @@ def peaks():
 # DRAM traffic of the tensor-core mode kernel from the ncu capture summarised in
 # profiles/mode_kernel_ws_convdiff3d_n128_ncu_full.md (one launch of the z-mode node pass:
 # 11 vectors x N unknowns); valid only while the kernel source is the one captured.
-PROFILED_MODE_TRAFFIC = {"source_sha256_16": "dc42b2fa54354838", "bytes": 186.191872e6 + 128.318976e6,
+PROFILED_MODE_TRAFFIC = {"source_sha256_16": "e647c4ea2ff5ea89", "bytes": 186.070784e6 + 128.555008e6,
                          "vector_passes": 11, "N": 2097152}
 
 
