@@ -138,18 +138,33 @@ def peaks():
 
 # DRAM traffic of the tensor-core mode kernel from the ncu capture summarised in
 # profiles/mode_kernel_ws_convdiff3d_n128_ncu_full.md (one launch of the z-mode node pass:
-# 11 vectors x N unknowns); valid only while the kernel source is the one captured.
-PROFILED_MODE_TRAFFIC = {"source_sha256_16": "e647c4ea2ff5ea89", "bytes": 186.070784e6 + 128.555008e6,
+# 11 vectors x N unknowns); valid only while the kernel code is the one captured (hash of
+# tc_mode.cu without comments and blank lines, see code_hash).
+PROFILED_MODE_TRAFFIC = {"source_sha256_16": "a109ed270605a2db", "bytes": 186.070784e6 + 128.555008e6,
                          "vector_passes": 11, "N": 2097152}
+
+
+def code_hash(path: str) -> str:
+    """First 16 hex digits of the sha256 of a C++/CUDA source without its // comments (a
+    trailing comment is dropped when no string literal precedes it) and blank lines."""
+    import hashlib
+    kept = []
+    with open(path, encoding="utf-8") as f:
+        for ln in f:
+            code = ln.rstrip("\n")
+            if "//" in code:
+                head = code.split("//", 1)[0]
+                if '"' not in head:
+                    code = head
+            if code.strip():
+                kept.append(code.rstrip())
+    return hashlib.sha256("\n".join(kept).encode()).hexdigest()[:16]
 
 
 def mode_traffic_per_launch(N, vector_passes_per_launch):
     """dram read + write bytes per average mode launch, scaled from the capture by the number
     of (vector, mode) products a launch processes; None if the kernel changed since."""
-    import hashlib
-    path = os.path.join(ROOT, "paper_2211_00696_gb300", "csrc", "tc_mode.cu")
-    with open(path, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    h = code_hash(os.path.join(ROOT, "paper_2211_00696_gb300", "csrc", "tc_mode.cu"))
     ref = PROFILED_MODE_TRAFFIC
     if h != ref["source_sha256_16"] or N != ref["N"]:
         return None

@@ -30,10 +30,11 @@
 //   NORMAL (R = 1, contraction over the fastest axis):   D[i][row] = sum_k E[i][k] X[row][k]
 //       A = E (128 rows, zero-padded), B = X tile (128 rows).  TMEM lane = i, column = row;
 //       stores out[row][i] coalesced over lanes.
-// K (= n) is processed in chunks of 32 through a 2-stage shared-memory ring: while the
-// tensor cores work on chunk c, the producer threads cut chunk c+1 (with the raw values of
-// the following chunk -- or of the next tile's first chunk -- already in flight), and the E
-// slices of the chunk arrive by one asynchronous bulk copy (TMA) per chunk.  Operands use
+// K (= n) is processed in chunks of 32 through a shared-memory ring of stages (two in the
+// single-role kernel, up to three in the warp-specialised ones): while the tensor cores work
+// on chunk c, the producer threads cut the next chunks (with the raw values of the following
+// chunk -- or of the next tile's first chunk -- already in flight), and the E slices of each
+// chunk arrive by one asynchronous bulk copy (TMA).  Operands use
 // the 64-byte-swizzled K-major layout (one 64-byte row of 32 BF16 per operand row, its four
 // 16-byte pieces permuted by bits 1-2 of the row; SBO = 512 B between 8-row groups); the
 // no-swizzle canonical layout (8-row x 16-byte core matrices, LBO = 128 B) remains
