@@ -220,6 +220,43 @@ def cpu_reference_step(prob, v, s, m, tol):
     return Q.alg6_phiquadmv(prob.factors, prob.tau, v, prob.l_max, tol, s=s, m=m)
 
 
+def oracle_step_seconds(tol: float) -> float:
+    """One oracle step of the default workload at `tol`, timed (called in a child process that
+    was started with one BLAS / OpenMP thread)."""
+    prob = workload()
+    v = prob.vector()
+    from oracle import planner as PL
+    s, m, _ = PL.setup_quadrature(tol, prob.l_max, PL.alpha_inf(prob.factors, prob.tau))
+    t0 = time.perf_counter()
+    cpu_reference_step(prob, v, s, m, tol)
+    return time.perf_counter() - t0
+
+
+def oracle_single_thread(tol: float):
+    """unknowns/s of the oracle on one host core (a fresh interpreter with the thread counts
+    of BLAS and OpenMP set to 1 before numpy loads), or None if the child fails."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", f"import bench; print(bench.oracle_step_seconds({tol!r}))"],
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+        dt = float(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        return None
+    return workload().N / dt
+
+
+def host_cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (subprocess.SubprocessError, OSError):
+        pass
+    return "unknown"
+
+
 def run_reference(args):
     """The oracle's CPU restatement of Algorithms 1 and 6 (numpy/scipy float64), rank 0."""
     rank = int(os.environ.get("RANK", "0"))
@@ -516,7 +553,9 @@ def run_ours(args):
             line["cpu_baseline"] = {"value": prob.N / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": "one full step at the GPU arm's tolerance: "
                                               "oracle.quadrature.alg6_phiquadmv (same algorithm, "
-                                              "numpy/scipy float64, BLAS threads = cores)"}
+                                              "numpy/scipy float64, BLAS threads = cores)",
+                                    "single_thread_value": oracle_single_thread(tol),
+                                    "cpu_model": host_cpu_model()}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
