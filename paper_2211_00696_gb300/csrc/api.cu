@@ -702,16 +702,7 @@ int phikron_apply_combo(phikron_plan_t plan, const double* B, double* Out, void*
 // while vector j + 1 is copied in on one copy stream and the results of vector j - 1 are
 // copied out on another, so that both link directions and the GPU are busy at once.
 // Events order each reuse of a staging buffer after the work that last touched it.
-int phikron_apply_host_many(phikron_plan_t plan, const double* V_host, double* Out_host, int count, void* stream) {
-  clear_error();
-  if (!plan || !V_host || !Out_host || count < 1) {
-    set_error("phikron_apply_host_many: NULL argument or count < 1");
-    return PHIKRON_EINVAL;
-  }
-  Plan& P = plan->impl;
-  DeviceGuard dg(P.opts.device);
-  if (dg.rc != PHIKRON_OK) return dg.rc;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+static int host_many_enqueue(Plan& P, const double* V_host, double* Out_host, int count, cudaStream_t st) {
   const size_t in_elems = (size_t)P.N;
   const size_t out_elems = (size_t)P.N * (P.p + 1) * (P.opts.half_step ? 2 : 1);
   if (!P.dV2) {
@@ -748,10 +739,34 @@ int phikron_apply_host_many(phikron_plan_t plan, const double* V_host, double* O
                                 cudaMemcpyDeviceToHost, P.cp_out));
     PK_TRY_CUDA(cudaEventRecord(P.ev_out[b], P.cp_out));
   }
-  // `stream` is ordered after the last copy-out, then everything is complete on return
+  // `stream` is ordered after the last copy-out
   PK_TRY_CUDA(cudaStreamWaitEvent(st, P.ev_out[(count - 1) & 1], 0));
-  PK_TRY_CUDA(cudaStreamSynchronize(st));
-  PK_TRY_CUDA(cudaStreamSynchronize(P.cp_in));
+  return PHIKRON_OK;
+}
+
+int phikron_apply_host_many(phikron_plan_t plan, const double* V_host, double* Out_host, int count, void* stream) {
+  clear_error();
+  if (!plan || !V_host || !Out_host || count < 1) {
+    set_error("phikron_apply_host_many: NULL argument or count < 1");
+    return PHIKRON_EINVAL;
+  }
+  Plan& P = plan->impl;
+  DeviceGuard dg(P.opts.device);
+  if (dg.rc != PHIKRON_OK) return dg.rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int rc = host_many_enqueue(P, V_host, Out_host, count, st);
+  // whatever was enqueued (on success or after an error) finishes before the host buffers
+  // are handed back
+  const cudaError_t e0 = cudaStreamSynchronize(st);
+  const cudaError_t e1 = P.cp_in ? cudaStreamSynchronize(P.cp_in) : cudaSuccess;
+  const cudaError_t e2 = P.cp_out ? cudaStreamSynchronize(P.cp_out) : cudaSuccess;
+  if (rc != PHIKRON_OK) return rc;
+  for (cudaError_t e : {e0, e1, e2}) {
+    if (e != cudaSuccess) {
+      set_error(std::string("phikron_apply_host_many: ") + cudaGetErrorString(e));
+      return PHIKRON_ECUDA;
+    }
+  }
   return PHIKRON_OK;
 }
 
@@ -763,9 +778,14 @@ int phikron_apply_host(phikron_plan_t plan, const double* V_host, double* Out_ho
   if (dg.rc != PHIKRON_OK) return dg.rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   PK_TRY_CUDA(cudaMemcpyAsync(P.dV, V_host, sizeof(double) * P.N, cudaMemcpyHostToDevice, st));
+  int rc;
   {
     ProfScope ps(&P.prof);
-    PK_RET(apply_dispatch(P, 1, P.dV, P.dOut, st));
+    rc = apply_dispatch(P, 1, P.dV, P.dOut, st);
+  }
+  if (rc != PHIKRON_OK) {
+    cudaStreamSynchronize(st);  // the copy from V_host is done before V_host goes back
+    return rc;
   }
   PK_TRY_CUDA(cudaMemcpyAsync(Out_host, P.dOut, sizeof(double) * P.N * (P.p + 1) * (P.opts.half_step ? 2 : 1),
                               cudaMemcpyDeviceToHost, st));
