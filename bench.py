@@ -338,7 +338,7 @@ def run_allen_cahn(args):
     a, u0 = W.allen_cahn2d()
     fac = [a, a]
     N = u0.size
-    nsteps = args.steps if args.steps != 20 else 200
+    nsteps = args.steps
     st = torch.cuda.current_stream()
     res = {}
     for method, mid in (("euler", pk.ERK_EULER), ("rk2", pk.ERK_RK2)):
