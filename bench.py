@@ -220,6 +220,9 @@ def cpu_reference_step(prob, v, s, m, tol):
     return Q.alg6_phiquadmv(prob.factors, prob.tau, v, prob.l_max, tol, s=s, m=m)
 
 
+REF_BUDGET_S = 60.0   # timed oracle work of one --impl reference run
+
+
 def oracle_step_seconds(tol: float) -> float:
     """One oracle step of the default workload at `tol`, timed (called in a child process that
     was started with one BLAS / OpenMP thread)."""
@@ -268,22 +271,30 @@ def run_reference(args):
     tol = args.tol if args.tol > 0 else PRECISIONS[args.precision][1]
     from oracle import planner as PL
     s, m, _ = PL.setup_quadrature(tol, prob.l_max, PL.alpha_inf(prob.factors, prob.tau))
-    for _ in range(args.warmup):
+    # A step is one full oracle apply (~1-3 s on the host cores).  The run is bounded to about
+    # REF_BUDGET_S of timed work: the first warm-up step measures a step, the remaining warm-up
+    # steps are capped at 2, and at most REF_BUDGET_S / (step time) of the K steps are timed.
+    tw = time.perf_counter()
+    cpu_reference_step(prob, v, s, m, tol)
+    t_one = time.perf_counter() - tw
+    for _ in range(min(args.warmup, 3) - 1):
         cpu_reference_step(prob, v, s, m, tol)
+    k_eff = max(1, min(args.steps, int(REF_BUDGET_S / max(t_one, 1e-3))))
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(k_eff):
         cpu_reference_step(prob, v, s, m, tol)
-    dt = (time.perf_counter() - t0) / args.steps
+    dt = (time.perf_counter() - t0) / k_eff
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     val = prob.N / dt
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "steps": args.steps, "steps_timed": k_eff, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": prob.name, "N": prob.N, "l_max": 3,
                                             "tau": 1e-2, "tol": tol, "s": s, "m": m},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "full workload per step: oracle.quadrature.alg6_phiquadmv "
-                                       "(scipy expm + numpy tensordot mode products, float64)"},
+                             "sample": f"full workload per step (oracle.quadrature.alg6_phiquadmv: scipy "
+                                       f"expm + numpy tensordot mode products, float64); {k_eff} of the "
+                                       f"{args.steps} steps timed (~{REF_BUDGET_S:.0f} s budget)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
