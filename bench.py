@@ -223,6 +223,24 @@ def cpu_reference_step(prob, v, s, m, tol):
 REF_BUDGET_S = 60.0   # timed oracle work of one --impl reference run
 
 
+def max_over_ranks(values, device):
+    """Elementwise maximum of per-rank float values over the process group (identity for one
+    process); device: where the reduction tensor lives (CUDA for NCCL, CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(x) for x in values]
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_throughput(world: int, unknowns_per_step: int, steps: int, max_seconds: float) -> float:
+    """Whole-job unknowns/s of `world` independent replicas: all replicas' work over the slowest
+    replica's time (weak scaling; the driver computes efficiency from these values)."""
+    return world * unknowns_per_step * steps / max_seconds
+
+
 def oracle_step_seconds(tol: float) -> float:
     """One oracle step of the default workload at `tol`, timed (called in a child process that
     was started with one BLAS / OpenMP thread)."""
@@ -482,12 +500,10 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     tot = float(np.sum(step_ms)) * 1e-3
     if world > 1:
-        t = torch.tensor([tot], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
+        tot = max_over_ranks([tot], dev)[0]
         dist.barrier()
     ms_per_step = tot / args.steps * 1e3
-    value = world * prob.N * args.steps / tot
+    value = replica_throughput(world, prob.N, args.steps, tot)
     gpu_launches = int(sum(counted["launches"].values()))
 
     # per-kernel CUDA-event timing of the same steps (separate pass, same stream)
@@ -521,9 +537,7 @@ def run_ours(args):
     plan.apply_host_many_ptr(vh.data_ptr(), oh.data_ptr(), e2e_steps)
     e2e_s = (time.perf_counter() - te) / e2e_steps
     if world > 1:
-        t = torch.tensor([e2e_s, e2e_single_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s, e2e_single_s = float(t[0].item()), float(t[1].item())
+        e2e_s, e2e_single_s = max_over_ranks([e2e_s, e2e_single_s], dev)
 
     line = None
     if rank == 0:
