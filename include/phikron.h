@@ -69,7 +69,13 @@ extern "C" {
                                          while its partial sums stay below 2^24 units; for
                                          long contractions (n[d] in the hundreds and more)
                                          the leading levels round at ~2^-24 of their partial
-                                         sums, which bounds the accuracy of that mode.      */
+                                         sums, which bounds the accuracy of that mode.
+                                         Mode kernel: warp-specialised by default; the
+                                         environment variable PHIKRON_MODE_KERNEL = "db"
+                                         (double-buffered TMEM, used where every n[d] >= 64)
+                                         or "classic" (single-role) selects another variant
+                                         for plans created afterwards; all three give the
+                                         same results up to FP32 accumulation order.       */
 
 #define PHIKRON_SELECT_PAPER      0   /* (s, m) from Algorithm 5                            */
 #define PHIKRON_SELECT_MLP        1   /* (s, m) from the learned selector, checked a posteriori,
