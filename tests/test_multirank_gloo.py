@@ -68,3 +68,18 @@ def test_reference_arm_is_rank0_only(monkeypatch, capsys):
 
     assert bench.run_reference(A()) is None
     assert capsys.readouterr().out == ""
+
+
+def test_code_hash_ignores_comments_only(tmp_path):
+    """The roofline traffic reference stays valid across comment edits of the kernel source and
+    becomes invalid when code changes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    c = tmp_path / "c.cu"
+    a.write_text('// header\nint f(int x) {\n  return x + 1;  // add one\n}\n\nconst char* s = "a // b";\n')
+    b.write_text('// other header\n\nint f(int x) {\n  return x + 1;\n}\nconst char* s = "a // b";\n')
+    c.write_text('// header\nint f(int x) {\n  return x + 2;  // add one\n}\n\nconst char* s = "a // b";\n')
+    assert bench.code_hash(str(a)) == bench.code_hash(str(b))
+    assert bench.code_hash(str(a)) != bench.code_hash(str(c))
