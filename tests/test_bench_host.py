@@ -1,7 +1,8 @@
-"""The N > 1 host logic of bench.py on CPU: two gloo ranks (127.0.0.1) reduce their timings to
-the maximum over ranks, the whole-job throughput of independent replicas is all ranks' work
-over the slowest rank's time, and the reference arm does nothing on ranks other than 0.
-The apply itself does not shard (replicas only), so these are the only multi-rank steps."""
+"""Host logic of bench.py on the CPU.  N > 1: two gloo ranks (127.0.0.1) reduce their timings
+to the maximum over ranks, the whole-job throughput of independent replicas is all ranks' work
+over the slowest rank's time, and the reference arm does nothing on ranks other than 0 (the
+apply itself does not shard -- replicas only -- so these are the only multi-rank steps).
+Roofline: the kernel code hash behind the traffic reference ignores comments."""
 import os
 import socket
 import sys
