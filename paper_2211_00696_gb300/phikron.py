@@ -195,7 +195,8 @@ def clenshaw_curtis(n: int):
 # ----------------------------------------------------------------------------- plans
 
 class Plan:
-    """phikron_plan_t owner.  ``factors``: list of 2 or 3 square float64 arrays (host)."""
+    """phikron_plan_t owner.  ``factors``: list of 1 to 6 square float64 arrays (host), one per
+    dimension of the Kronecker sum."""
 
     def __init__(self, factors, tau: float, l_max: int, tol: float, *, precision: int = PREC_FP64,
                  quad: int = QUAD_GAUSS, force_s: int = -1, force_m: int = -1, alpha: float = 0.0,
