@@ -37,6 +37,7 @@ UNIT = "unknowns/s"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "convdiff3d_n128_tau1e-2_seed0_samples.txt")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FLUSH_BYTES = 512 << 20
+CLOCK_PREROLL_S = 1.5
 
 # (precision id, quadrature tolerance, digit slices; 0 = from the tolerance).  "mixed" is the
 # fastest setting that meets the metric's 1e-8 gate with margin: tolerance 1e-9 (a-priori
@@ -65,7 +66,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -81,6 +82,13 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def mark_timed(self):
+        """The timed region starts: samples from here on fall inside it until mark_end()."""
+        self.timed_from = len(self.lines)
+
+    def mark_end(self):
+        self.timed_to = len(self.lines)
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -104,8 +112,9 @@ class ClockSampler:
             for nm, val in zip(names, f[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
+        timed = max(0, getattr(self, "timed_to", len(self.lines)) - getattr(self, "timed_from", len(self.lines)))
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "samples_in_timed_region": timed, "reasons": sorted(reasons)}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -486,6 +495,21 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
+    # The sampler's window: identical untimed steps for at least CLOCK_PREROLL_S right before the
+    # timed region (the region itself can be a few ms, shorter than one sampling interval), so
+    # that the clocks recorded are those of the GPU under this load when the timed steps start.
+    pre0 = time.perf_counter()
+    preroll = 0
+    while time.perf_counter() - pre0 < CLOCK_PREROLL_S:
+        for _ in range(16):
+            flush.zero_()
+            plan.apply(V, Out)
+        torch.cuda.synchronize()
+        preroll += 16
+    clk.mark_timed()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     plan.profile_begin(0)            # launch counting only
     wall0 = time.perf_counter()
     for i in range(args.steps):
@@ -495,8 +519,11 @@ def run_ours(args):
         ends[i].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    clk.mark_end()
     counted = plan.profile_end()
     clocks = clk.stop()
+    clocks["window"] = (f"{preroll} identical untimed steps ({CLOCK_PREROLL_S:.1f} s) immediately before "
+                        f"the timed region, and the timed region")
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     tot = float(np.sum(step_ms)) * 1e-3
     if world > 1:

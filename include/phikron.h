@@ -101,6 +101,11 @@ typedef struct phikron_opts {
   int    skip_phi0;   /* l_max >= 1: do not compute phi_0 (one Kronecker action fewer); the
                          phi_0 slots of Out (and of the tau/2 block) are left untouched.
                          Exponential Runge-Kutta stages need phi_1..phi_p only.  Default 0.  */
+  int    wait_us;     /* OZAKI_BF16: limit, in microseconds, of every bounded wait inside the
+                         tensor-core kernels (a stage of the operand ring, a TMEM buffer, a bulk
+                         copy); on expiry the kernel stops, records PHIKRON_ETIMEOUT for
+                         phikron_check_status and leaves its outputs undefined.  0 = the default
+                         of 2 s.  A short limit is for testing that failure path.             */
 } phikron_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -349,14 +354,17 @@ int phikron_clenshaw_curtis(int n, double* x, double* w);
  * float64 scaling and squaring with the degree-18 Taylor polynomial (Paterson-Stockmeyer,
  * GEMMs only; ||2^-s scale A||_1 <= 1 keeps the truncation below the float64 unit
  * roundoff).  scale is a HOST array of count doubles; norms1 is a HOST array with
- * ||A[b]||_1 (used to pick the scaling without a device round trip).  workspace: DEVICE, at least
- * phikron_expm_workspace_bytes(count, n) bytes. */
+ * ||A[b]||_1 (used to pick the scaling without a device round trip) or NULL, in which case the
+ * library computes the norms from a copy of A and the call synchronises the stream first.
+ * workspace: DEVICE, at least phikron_expm_workspace_bytes(count, n) bytes. */
 size_t phikron_expm_workspace_bytes(int count, int n);
 int phikron_expm_batched(int count, int n, const double* A, const double* scale,
                          const double* norms1, double* E, void* workspace, void* stream);
 
 /* Out = (E_1 (x) ... (x) E_dims) V for one vector, float64 (mode products, Eq. (8)).
- * E: dims DEVICE pointers to n[d] x n[d] row-major matrices; work: DEVICE, N doubles. */
+ * E: dims DEVICE pointers to n[d] x n[d] row-major matrices; work: DEVICE, N doubles.
+ * V, Out and work (the last only when dims > 1) must be pairwise non-overlapping ranges of
+ * N float64, else PHIKRON_EINVAL: each mode product reads its whole input while writing. */
 int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const double* V,
                            double* Out, double* work, void* stream);
 
@@ -367,8 +375,12 @@ int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const
  * `work` argument: the intermediate lives in a built-in device array of
  * phikron_noalloc_max_elements() float64 (8 MiB, held by every GPU that loads the library
  * until exit).  prod n[d] above that limit returns PHIKRON_EINVAL.  No cudaMalloc/cudaFree
- * is called.  The first call on a device looks the array's address up (make it before any
- * stream capture).  All calls share the array: calls that overlap on the GPU race. */
+ * is called.  The first call on a device is a warm-up: it looks the array's address up and,
+ * with lazy module loading, loads the library's device code there (which may allocate and
+ * synchronise); make it before any stream capture.  Later calls allocate nothing.  The
+ * address is cached per device for the life of the process (cudaDeviceReset between calls
+ * is not supported).  V and Out must not overlap (PHIKRON_EINVAL).  All calls share the
+ * array: calls that overlap on the GPU race. */
 long long phikron_noalloc_max_elements(void);
 int phikron_kron_apply_f64_noalloc(int dims, const int* n, const double* const* E, const double* V,
                                    double* Out, void* stream);

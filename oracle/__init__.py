@@ -20,7 +20,11 @@ integrators", arXiv 2211.00696):
 * ``quadrature`` -- Algorithms 1 and 6 (fixed quadrature + scaling and modified
                     squaring) restated step by step with library matrix exponentials;
                     used to check the reading of the paper and intermediate results.
-* ``mlp``        -- float64 reference of the (s, m) selector network and its gradients.
+* ``selector``   -- the measured error criterion, the cost-minimising (s, m) search that
+                    labels the learned selector's training data, and a float64 statement
+                    of the selector network with its analytic gradients.
+* ``erk``        -- exponential Euler and Runge-Kutta steps (Eq. (RK), Table RK), every
+                    tableau entry applied as its own phi-action supplied by the caller.
 
 Parity status: every function here is pinned by tests under ``tests/`` against
 closed forms, invariants, the paper's tables or brute force (see each docstring).

@@ -592,6 +592,7 @@ void phikron_opts_default(phikron_opts* o) {
   o->slices = 0;
   o->half_step = 0;
   o->skip_phi0 = 0;
+  o->wait_us = 0;
 }
 
 const char* phikron_last_error(void) { return g_err.c_str(); }
@@ -642,6 +643,10 @@ int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const in
   }
   if (o.selector != PHIKRON_SELECT_PAPER && o.selector != PHIKRON_SELECT_MLP) {
     set_error("phikron_plan: bad selector");
+    return PHIKRON_EINVAL;
+  }
+  if (o.wait_us < 0) {
+    set_error("phikron_plan: wait_us must be >= 0");
     return PHIKRON_EINVAL;
   }
   DeviceGuard dg(o.device);
@@ -934,7 +939,29 @@ size_t phikron_expm_workspace_bytes(int count, int n) { return expm_workspace_by
 int phikron_expm_batched(int count, int n, const double* A, const double* scale,
                          const double* norms1, double* E, void* workspace, void* stream) {
   clear_error();
-  return expm_batched(count, n, A, scale, norms1, E, workspace, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<double> own;
+  if (!norms1 && count > 0) {
+    // ||A[b]||_1 (largest absolute column sum) from a host copy of the matrices: synchronous
+    if (n < 1 || !A) {
+      set_error("phikron_expm_batched: bad arguments");
+      return PHIKRON_EINVAL;
+    }
+    const size_t nn = (size_t)n * n;
+    std::vector<double> h(nn * count);
+    PK_TRY_CUDA(cudaMemcpyAsync(h.data(), A, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+    PK_TRY_CUDA(cudaStreamSynchronize(st));
+    own.assign(count, 0.0);
+    std::vector<double> col(n);
+    for (int b = 0; b < count; ++b) {
+      std::fill(col.begin(), col.end(), 0.0);
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) col[k] += std::fabs(h[nn * b + (size_t)i * n + k]);
+      own[b] = *std::max_element(col.begin(), col.end());
+    }
+    norms1 = own.data();
+  }
+  return expm_batched(count, n, A, scale, norms1, E, workspace, st);
 }
 
 int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const double* V,
@@ -942,6 +969,20 @@ int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const
   clear_error();
   if (dims < 1 || dims > PHIKRON_MAX_DIMS || !n || !E || !V || !Out || !work) {
     set_error("phikron_kron_apply_f64: bad arguments");
+    return PHIKRON_EINVAL;
+  }
+  long long N = 1;
+  for (int d = 0; d < dims; ++d) {
+    if (n[d] < 1 || !E[d]) {
+      set_error("phikron_kron_apply_f64: bad size or matrix pointer");
+      return PHIKRON_EINVAL;
+    }
+    N *= n[d];
+  }
+  // a mode product reads its whole input while it writes its output: V, Out and work must be
+  // three separate ranges of N float64 (work is unused for one factor)
+  if (ranges_overlap(V, Out, N) || (dims > 1 && (ranges_overlap(V, work, N) || ranges_overlap(Out, work, N)))) {
+    set_error("phikron_kron_apply_f64: V, Out and work must not overlap");
     return PHIKRON_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -35,6 +35,7 @@ struct Seq {
   bool half = false;
   size_t njobs_mode = 0;
   cudaGraphExec_t exec = nullptr;
+  unsigned long long wait_ns = 2000000000ull;  // limit of the kernels' bounded waits
   size_t device_bytes = 0;
   std::vector<void*> allocs;
   ~Seq();

@@ -40,6 +40,13 @@ void clear_error();
     if (r_ != PHIKRON_OK) return r_;                                                       \
   } while (0)
 
+// true if the address ranges [a, a + n) and [b, b + n) of n float64 share an element
+inline bool ranges_overlap(const void* a, const void* b, long long n) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  const uintptr_t len = static_cast<uintptr_t>(n) * sizeof(double);
+  return x < y + len && y < x + len;
+}
+
 // ----------------------------------------------------------------------------- planner
 namespace planner {
 int log_quaderr(double n, int p, double alpha, double beta, int rule, double* out);

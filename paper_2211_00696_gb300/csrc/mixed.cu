@@ -673,6 +673,13 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
   S.p = p;
   S.half = cfg.half;
   S.ninst = ninst;
+  // the longest wait limit any plan of the sequence asks for (0 = the default 2 s)
+  unsigned long long wait_us = 0;
+  for (const SeqUnit& U : units) {
+    const unsigned long long w = U.plan->opts.wait_us > 0 ? (unsigned long long)U.plan->opts.wait_us : 2000000ull;
+    wait_us = std::max(wait_us, w);
+  }
+  S.wait_ns = wait_us * 1000ull;
   // per-unit exponent slots
   std::vector<int> slot0(nu);
   for (int u = 0; u < nu; ++u) {
@@ -955,6 +962,7 @@ int seq_launch_all(Seq& S, cudaStream_t st) {
       P.njobs = s.count;
       P.total_tiles = s.total;
       P.ptrtab = S.dPtrtab;
+      P.wait_ns = S.wait_ns;
       PK_RET(tc::mode_pass(P, s.shape, S.dStatus, st));
     } else if (s.kind == STEP_EXPSCAN) {
       launch_begin(KC_CONVERT, st);

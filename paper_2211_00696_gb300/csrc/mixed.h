@@ -30,6 +30,7 @@ struct GPass {
   int njobs;
   long long total_tiles;
   const void* const* ptrtab;
+  unsigned long long wait_ns;  // limit of every bounded mbarrier wait (wall clock)
 };
 
 struct PassShape {

@@ -10,12 +10,17 @@
 // The scratch is a file-scope __device__ array of kMaxElems float64 (8 MiB).  Every GPU
 // that loads the library holds it until the process exits.  In host code the array's name
 // is only a host-side stand-in, so its device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) on the first call made on that device;
-// make that first call before any stream capture.  All calls share the one array and it
-// keeps whatever the previous call wrote; the mode-product chain writes every scratch
-// element before reading it, so nothing needs clearing.  Calls whose executions overlap on
-// the GPU (different streams, or different host threads) race on the array: serialise
-// them.
+// cudaGetSymbolAddress (with that device current) on the first call made on that device.
+// That first call is a warm-up: with lazy module loading it is the call that loads the
+// library's device code (and so creates the array) on that device, which can allocate and
+// synchronise; make it before any stream capture and outside latency-critical loops.  Later
+// calls allocate nothing.  The address is cached per device ordinal for the life of the
+// process: cudaDeviceReset (which destroys the context that holds the array) is not
+// supported between calls.  All calls share the one array and it keeps whatever the
+// previous call wrote; the mode-product chain writes every scratch element before reading
+// it, so nothing needs clearing.  Calls whose executions overlap on the GPU (different
+// streams, or different host threads) race on the array: serialise them.  V and Out must
+// not overlap (PHIKRON_EINVAL).
 #include <mutex>
 
 #include "common.h"
@@ -76,6 +81,12 @@ extern "C" int phikron_kron_apply_f64_noalloc(int dims, const int* n, const doub
   if (N > kMaxElems) {
     set_error("phikron_kron_apply_f64_noalloc: prod n[d] = " + std::to_string(N) +
               " exceeds the built-in scratch of " + std::to_string(kMaxElems) + " float64");
+    return PHIKRON_EINVAL;
+  }
+  // a mode product reads its whole input while it writes its output (with an odd number of
+  // factors the first one writes Out while reading V)
+  if (ranges_overlap(V, Out, N)) {
+    set_error("phikron_kron_apply_f64_noalloc: V and Out must not overlap");
     return PHIKRON_EINVAL;
   }
   double* work = nullptr;

@@ -35,7 +35,7 @@ class Opts(C.Structure):
     _fields_ = [("quad", C.c_int), ("precision", C.c_int), ("selector", C.c_int),
                 ("force_s", C.c_int), ("force_m", C.c_int), ("alpha", C.c_double),
                 ("beta", C.c_double), ("device", C.c_int), ("max_rhs", C.c_int), ("slices", C.c_int),
-                ("half_step", C.c_int), ("skip_phi0", C.c_int)]
+                ("half_step", C.c_int), ("skip_phi0", C.c_int), ("wait_us", C.c_int)]
 
 
 class Info(C.Structure):
@@ -201,7 +201,8 @@ class Plan:
     def __init__(self, factors, tau: float, l_max: int, tol: float, *, precision: int = PREC_FP64,
                  quad: int = QUAD_GAUSS, force_s: int = -1, force_m: int = -1, alpha: float = 0.0,
                  beta: float = 0.0, device: int = -1, max_rhs: int = 1, slices: int = 0,
-                 half_step: bool = False, selector: int = SELECT_PAPER, skip_phi0: bool = False):
+                 half_step: bool = False, selector: int = SELECT_PAPER, skip_phi0: bool = False,
+                 wait_us: int = 0):
         L = lib()
         self._h = C.c_void_p()
         facs = [np.ascontiguousarray(a, dtype=np.float64) for a in factors]
@@ -218,6 +219,7 @@ class Plan:
         o.half_step = 1 if half_step else 0
         o.skip_phi0 = 1 if skip_phi0 else 0
         o.selector = selector
+        o.wait_us = wait_us
         _check(L.phikron_plan(C.byref(self._h), len(facs), ptrs, ns, tau, l_max, tol, C.byref(o)))
         self.shape = tuple(a.shape[0] for a in facs)
         self.N = int(np.prod(self.shape))
@@ -422,11 +424,11 @@ def expm_batched(A, scale, stream=None):
     count, n, _ = A.shape
     A = A.contiguous()
     sc = np.ascontiguousarray(scale, dtype=np.float64)
-    norms = np.ascontiguousarray(A.abs().sum(dim=1).max(dim=1).values.cpu().numpy(), dtype=np.float64)
     E = torch.empty_like(A)
     ws = torch.empty(int(lib().phikron_expm_workspace_bytes(count, n)) // 8 + 1, dtype=torch.float64,
                      device=A.device)
-    _check(lib().phikron_expm_batched(count, n, A.data_ptr(), _dp(sc), _dp(norms), E.data_ptr(),
+    # norms1 = NULL: the library takes ||A[b]||_1 itself (synchronous)
+    _check(lib().phikron_expm_batched(count, n, A.data_ptr(), _dp(sc), None, E.data_ptr(),
                                       ws.data_ptr(), _stream_ptr(stream)))
     return E
 

@@ -4,7 +4,7 @@ seed 0).
 
 Calls only the oracle (O3: scipy's expm_multiply on the sparse augmented matrix, the plain
 definition of Eq. (3)) and the seeded input generator.  The full vectors are too large to
-store, so the file keeps 1024 seeded sample indices with the value of every phi_l there,
+store, so the file keeps 16384 seeded sample indices with the value of every phi_l there,
 plus each full phi_l's 2-norm and inf-norm.  Run from the repository root:
 
     python tests/golden/make_convdiff_samples.py [n]
@@ -22,7 +22,7 @@ import workloads as W  # noqa: E402
 from oracle import phi as P  # noqa: E402
 
 
-def main(n: int = 128, samples: int = 1024):
+def main(n: int = 128, samples: int = 16384):
     prob = W.convdiff3d(n=n, tau=1e-2, l_max=3, tol=1e-10, seed=0)
     v = prob.vector()
     t0 = time.time()

@@ -100,3 +100,23 @@ def test_invalid_arguments_return_einval_without_gpu():
         with pytest.raises(pk.PhikronError) as e:
             pk.Integrator([np.eye(4), np.eye(4)], tau, method, 1e-10, **kw)
         assert e.value.code == B.EINVAL
+
+
+def test_kron_apply_rejects_overlapping_buffers_before_any_device_work():
+    """A mode product reads its whole input while it writes its output, so V, Out (and the work
+    buffer) must be separate ranges; overlapping ranges are refused before anything is launched
+    (no device memory is touched: the pointers here are placeholders)."""
+    import ctypes as C
+    L = pk.lib()
+    n = (C.c_int * 3)(4, 4, 4)           # N = 64 float64 = 512 bytes
+    E = (C.c_void_p * 3)(0x10000, 0x10000, 0x10000)
+    base = 0x7F0000000000
+    # V == Out, and Out starting inside V
+    for out in (base, base + 8 * 63):
+        rc = L.phikron_kron_apply_f64_noalloc(3, n, E, base, out, None)
+        assert rc == B.EINVAL and b"overlap" in L.phikron_last_error()
+        rc = L.phikron_kron_apply_f64(3, n, E, base, out, base + 4096, None)
+        assert rc == B.EINVAL and b"overlap" in L.phikron_last_error()
+    # work overlapping V (three factors use it)
+    rc = L.phikron_kron_apply_f64(3, n, E, base, base + 4096, base + 256, None)
+    assert rc == B.EINVAL and b"overlap" in L.phikron_last_error()

@@ -14,6 +14,13 @@ import pytest
 import workloads as W
 from oracle import phi as P
 
+# The uneven batched workload's accuracy statement: plans at tolerance CONFIG3_TOL with
+# CONFIG3_SLICES digit slices per operand; every output within CONFIG3_GATE relative 2-norm
+# error of the spectral oracle.
+CONFIG3_TOL = 1e-6
+CONFIG3_SLICES = 3
+CONFIG3_GATE = 1e-6
+
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
@@ -110,10 +117,11 @@ def test_batched_uneven_matches_single_and_spectral(autotune):
 
 def test_config3_full_size_batched():
     """32 instances, (n_x, n_y, n_z) from {64, 96, 128, 192, 256}, c ~ U(0.1, 1),
-    tau ~ logU(1e-4, 1e-1), 4 right-hand sides, phi_0..phi_3 at tau and tau/2, FP32-class
-    digit products (3 slices) with float64 exponentials; autotuned grouped launches in one
-    graph.  Checked: the smallest, a middle and the largest instance against the spectral
-    oracle (all 4 RHS x 8 outputs of the smallest, RHS 0 of the others), and every output
+    tau ~ logU(1e-4, 1e-1), 4 right-hand sides, phi_0..phi_3 at tau and tau/2, digit products
+    with float64 exponentials and float-float recurrence; autotuned grouped launches in one
+    graph.  Checked against the spectral oracle: right-hand side 0 of every instance (8
+    outputs each) and all 4 right-hand sides of the smallest instance, at the workload's
+    stated tolerance CONFIG3_GATE (relative 2-norm error per output), plus every output
     finite."""
     pk = _pk()
     insts = W.batched_uneven3d()
@@ -122,8 +130,8 @@ def test_config3_full_size_batched():
     free, _ = torch.cuda.mem_get_info()
     if free < need:
         pytest.skip(f"needs ~{need / 2**30:.0f} GiB of device memory, {free / 2**30:.0f} GiB free")
-    plans = [pk.Plan(W.batched_instance_factors(d), d["tau"], 3, 1e-6, precision=pk.PREC_OZAKI_BF16,
-                     slices=3, half_step=True) for d in insts]
+    plans = [pk.Plan(W.batched_instance_factors(d), d["tau"], 3, CONFIG3_TOL, precision=pk.PREC_OZAKI_BF16,
+                     slices=CONFIG3_SLICES, half_step=True) for d in insts]
     batch = pk.Batch(plans, nrhs=4, half_step=True, autotune=True)
     V = [torch.stack([torch.from_numpy(W.uniform_vector(d["shape"], s)) for s in d["rhs_seeds"]]).cuda()
          for d in insts]
@@ -132,15 +140,17 @@ def test_config3_full_size_batched():
     assert batch.info()["tuned"] == 1
     for o in out:
         assert bool(torch.isfinite(o).all())
-    order = np.argsort(N)
-    for rank, i in enumerate([order[0], order[len(order) // 2], order[-1]]):
-        d = insts[i]
-        rhs_list = range(4) if rank == 0 else [0]
-        for r in rhs_list:
+    smallest = int(np.argmin(N))
+    worst = []
+    for i, d in enumerate(insts):
+        for r in (range(4) if i == smallest else [0]):
             v = V[i][r].cpu().numpy()
             got = out[i][r].cpu().numpy()
             full = P.phi_spectral_dirichlet(d["shape"], [d["coeff"]] * 3, d["tau"], v, 3)
             half = P.phi_spectral_dirichlet(d["shape"], [d["coeff"]] * 3, d["tau"] / 2, v, 3)
-            for l in range(4):
-                assert P.rel_err_2(got[l], full[l]) <= 2e-5, (i, r, l)
-                assert P.rel_err_2(got[4 + l], half[l]) <= 2e-5, (i, r, l)
+            e = max(max(P.rel_err_2(got[l], full[l]) for l in range(4)),
+                    max(P.rel_err_2(got[4 + l], half[l]) for l in range(4)))
+            worst.append((e, i, r, d["shape"], plans[i].info()["s"]))
+    worst.sort(reverse=True)
+    print("config 3 largest errors (err, instance, rhs, shape, s):", worst[:5])
+    assert worst[0][0] <= CONFIG3_GATE, worst[:5]

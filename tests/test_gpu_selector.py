@@ -102,8 +102,12 @@ def test_training_reduces_loss_and_predicts_labels():
 
 @pytest.mark.parametrize("tol,slices", [(1e-6, 4), (1e-10, 5)])
 def test_selector_gain_on_256_cubed(tol, slices):
-    """The network's (s, m) costs no more than Algorithm 5's on a 256^3 reaction-diffusion
-    Laplacian and both meet the tolerance against the spectral oracle."""
+    """On a 256^3 reaction-diffusion Laplacian the network's (s, m) costs strictly less than
+    Algorithm 5's (fewer Kronecker actions), its apply is faster, and both meet the tolerance
+    against the spectral oracle.  The tolerance is checked in the sense both selectors plan
+    for: the a-posteriori criterion bounds the 2-norm error relative to ||v||_2, so the gate is
+    ||phi_l(-tau A)v - out_l||_2 <= tol * ||v||_2 for every l (a relative error against
+    ||phi_l v||_2, which is smaller than ||v||_2, can exceed tol without the plan being wrong)."""
     pk = _pk()
     src = _trained_model(pk)
     shape, coeff, tau, p = (256, 256, 256), 0.05, 1e-3, 3
@@ -125,15 +129,17 @@ def test_selector_gain_on_256_cubed(tol, slices):
         e1.record(st)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
-        errs = [P.rel_err_2(got[l], exact[l]) for l in range(p + 1)]
+        errs = [float(np.linalg.norm(got[l] - exact[l]) / np.linalg.norm(v)) for l in range(p + 1)]
         res[sel] = (info, e0.elapsed_time(e1) / 3, errs)
         plan.close()
     (ip, tp, ep), (im, tm, em) = res[pk.phikron.SELECT_PAPER], res[pk.phikron.SELECT_MLP]
     print(f"model={src} tol={tol}: paper (s,m,C)=({ip['s']},{ip['m']},{ip['cost']}) {tp:.3f} ms err {max(ep):.2e}; "
           f"mlp (s,m,C)=({im['s']},{im['m']},{im['cost']}) used={im['selector_used']} {tm:.3f} ms err {max(em):.2e}")
     assert im["selector_used"] in (1, 2)
-    assert im["cost"] <= ip["cost"]
-    assert max(ep) <= 2 * tol + 1e-12 and max(em) <= 2 * tol + 1e-12
+    assert im["cost"] < ip["cost"], (im["cost"], ip["cost"])
+    assert im["actions"] < ip["actions"]
+    assert tm < tp, (tm, tp)
+    assert max(ep) <= tol and max(em) <= tol, (ep, em)
 
 
 def test_selector_fallbacks():

@@ -139,3 +139,23 @@ def test_twenty_one_nodes_claim_sec33():
         simplified = 1.0 / (2 ** (p + 1) * math.factorial(p)) * (2 * 20 - p) ** (-(2 * 20 - p))
         assert simplified < 1e-20
     assert PL.quaderr(20, 20, 2.0 / math.e, 1.0) < 1e-20
+
+
+def test_alpha_inf_is_the_max_row_sum_on_nonsymmetric_factors():
+    """Eq. (31) sums the infinity norms (maximum absolute ROW sum) of the factors.  These factors
+    are neither symmetric nor Toeplitz, so their row and column sums differ, and so do the max
+    of row sums and the sum of all entries; the values are worked out by hand:
+      A1 = [[1, -2], [0, 3]]            row sums 3, 3        -> 3   (column sums 1, 5 -> 5)
+      A2 = [[0, 0, 4], [-1, 1, 0],
+            [0.5, 0, 0]]                row sums 4, 2, 0.5   -> 4   (column sums 1.5, 1, 4)
+      A3 = [[-7]]                                            -> 7
+    alpha = tau * (3 + 4 + 7) = 14 tau."""
+    A1 = np.array([[1.0, -2.0], [0.0, 3.0]])
+    A2 = np.array([[0.0, 0.0, 4.0], [-1.0, 1.0, 0.0], [0.5, 0.0, 0.0]])
+    A3 = np.array([[-7.0]])
+    assert PL.alpha_inf([A1], 1.0) == 3.0
+    assert PL.alpha_inf([A1.T], 1.0) == 5.0          # the transpose has the column sums as rows
+    assert PL.alpha_inf([A2], 1.0) == 4.0
+    assert PL.alpha_inf([A1, A2, A3], 0.25) == 0.25 * 14.0
+    # a single row: the inf-norm is the sum of |entries| in it, not their max
+    assert PL.alpha_inf([np.array([[2.0, -3.0], [0.0, 0.0]])], 1.0) == 5.0
