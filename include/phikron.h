@@ -75,7 +75,16 @@ extern "C" {
                                          (double-buffered TMEM, used where every n[d] >= 64)
                                          or "classic" (single-role) selects another variant
                                          for plans created afterwards; all three give the
-                                         same results up to FP32 accumulation order.       */
+                                         same results up to FP32 accumulation order.
+                                         Node weights: with the environment variable
+                                         PHIKRON_FUSED_WEIGHTS = "1" at plan time, and where
+                                         1 <= l_max <= 4, dims >= 2 and the last factor has
+                                         n <= 128, the last mode pass of the node phase also
+                                         forms the weighted sums of Algorithm 1 in its epilogue
+                                         (one tile of 32 fibers runs every node and keeps the
+                                         l_max float-float sums in TMEM), with bitwise the
+                                         results of the separate weighted-sum pass.  Off by
+                                         default: the separate passes are faster.           */
 
 #define PHIKRON_SELECT_PAPER      0   /* (s, m) from Algorithm 5                            */
 #define PHIKRON_SELECT_MLP        1   /* (s, m) from the learned selector, checked a posteriori,
@@ -211,6 +220,9 @@ typedef struct phikron_info {
   int    slices;       /* digit slices of the mixed path (0 for FP64)                   */
   int    adaptive_nodes;  /* PHIKRON_QUAD_CC_ADAPTIVE: nodes used by the last apply (0 before)  */
   double adaptive_err;    /* and its final error estimate (Algorithm 2's err)                  */
+  int    fused_weights;   /* OZAKI_BF16: 1 if the apply folds Algorithm 1's node weights into the
+                             last mode pass of the node phase (no node product T_k is written to
+                             device memory; PHIKRON_FUSED_WEIGHTS = "1"), else 0               */
 } phikron_info;
 
 int  phikron_plan_info(phikron_plan_t plan, phikron_info* info);
@@ -324,6 +336,14 @@ int phikron_profile_end(phikron_plan_t plan, phikron_profile* out);
 
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* phikron_last_error(void);
+
+/* Device buffers the library holds right now for plans, launch sequences, batches and
+ * integrators (process-wide): every failing create call frees what it allocated, so this
+ * returns to its previous value after one.  Fault injection for tests of those paths: with the
+ * environment variable PHIKRON_FAIL_ALLOC_AFTER = k, the library's host object and device
+ * buffer allocations after the first k (counted from when the variable took that value) are
+ * refused and the call returns PHIKRON_ENOMEM; unset it to allocate normally. */
+long long phikron_live_device_buffers(void);
 
 /* ------------------------------------------------------------------ planner (host only)
  * Algorithms 3-5 of Sec. 3.2-3.3, exposed so the planner can be checked without a GPU.

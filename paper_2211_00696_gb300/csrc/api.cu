@@ -1,9 +1,12 @@
 // C ABI of libphikron: plan construction (Algorithm 6's set-up) and the apply path
 // (Algorithm 1 on 2^{-s}M, s modified-squaring steps of Eq. (29), phi_0 by Eq. (8)).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -75,18 +78,58 @@ Plan::~Plan() {
     if (e) cudaEventDestroy(e);
   if (cp_in) cudaStreamDestroy(cp_in);
   if (cp_out) cudaStreamDestroy(cp_out);
-  for (void* p : allocations) cudaFree(p);
+  for (void* p : allocations) device_free(p);
   if (mixed && mixed_free) mixed_free(mixed);
+}
+
+bool alloc_fault() {
+  static std::mutex mu;
+  static std::string seen;
+  static long long count = 0;
+  const char* v = std::getenv("PHIKRON_FAIL_ALLOC_AFTER");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!v || !*v) {
+    seen.clear();
+    return false;
+  }
+  if (seen != v) {   // a new setting restarts the count
+    seen = v;
+    count = 0;
+  }
+  const long long k = std::atoll(v);
+  return count++ >= k;
+}
+
+std::atomic<long long> g_live_buffers{0};
+
+void device_free(void* p) {
+  if (!p) return;
+  cudaFree(p);
+  g_live_buffers.fetch_sub(1);
+}
+
+int device_malloc(void** p, size_t bytes, const char* who) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (alloc_fault()) {
+    set_error(std::string(who) + ": device allocation of " + std::to_string(bytes) +
+              " bytes refused (PHIKRON_FAIL_ALLOC_AFTER)");
+    return PHIKRON_ENOMEM;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error(std::string(who) + ": cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    return PHIKRON_ENOMEM;
+  }
+  g_live_buffers.fetch_add(1);
+  return PHIKRON_OK;
 }
 
 int Plan::alloc(void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
-    return PHIKRON_ENOMEM;
-  }
+  PK_RET(device_malloc(p, bytes, "phikron_plan"));
   allocations.push_back(*p);
   device_bytes += bytes;
   return PHIKRON_OK;
@@ -374,7 +417,7 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
     PK_TRY_CUDA(cudaStreamSynchronize(st));
     // staging for the expm is no longer needed
     for (void* q : {(void*)dIn, (void*)dOut, ws}) {
-      cudaFree(q);
+      device_free(q);
       P.allocations.erase(std::find(P.allocations.begin(), P.allocations.end(), q));
     }
     P.device_bytes -= sizeof(double) * nn * cnt * 2 + expm_workspace_bytes(cnt, nd);
@@ -597,6 +640,8 @@ void phikron_opts_default(phikron_opts* o) {
 
 const char* phikron_last_error(void) { return g_err.c_str(); }
 
+long long phikron_live_device_buffers(void) { return phikron::g_live_buffers.load(); }
+
 int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const int* n, double tau,
                  int l_max, double tol, const phikron_opts* opts) {
   clear_error();
@@ -652,9 +697,15 @@ int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const in
   DeviceGuard dg(o.device);
   if (dg.rc != PHIKRON_OK) return dg.rc;
   if (cudaGetDevice(&o.device) != cudaSuccess) { set_error("cudaGetDevice failed"); return PHIKRON_ECUDA; }
-  phikron_plan_s* h = new (std::nothrow) phikron_plan_s();
+  phikron_plan_s* h = alloc_fault() ? nullptr : new (std::nothrow) phikron_plan_s();
   if (!h) { set_error("phikron_plan: host allocation failed"); return PHIKRON_ENOMEM; }
-  int rc = build_plan(h->impl, dims, A, n, tau, l_max, tol, o);
+  int rc;
+  try {
+    rc = build_plan(h->impl, dims, A, n, tau, l_max, tol, o);
+  } catch (const std::bad_alloc&) {
+    set_error("phikron_plan: host allocation failed");
+    rc = PHIKRON_ENOMEM;
+  }
   if (rc != PHIKRON_OK) {
     delete h;
     return rc;
@@ -822,6 +873,7 @@ int phikron_plan_info(phikron_plan_t plan, phikron_info* info) {
   info->adaptive_nodes = P.last_nodes;
   info->adaptive_err = P.last_err;
   info->slices = P.mixed ? mixed_slices(P) : 0;
+  info->fused_weights = mixed_fused(P) ? 1 : 0;
   return PHIKRON_OK;
 }
 

@@ -29,19 +29,14 @@ struct phikron_batch_s {
   bool tuned = false;
   ~phikron_batch_s() {
     cand.clear();
-    for (void* p : work) cudaFree(p);
+    for (void* p : work) device_free(p);
   }
 };
 
 namespace {
 
 int walloc(phikron_batch_s& B, void** p, size_t bytes) {
-  const cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_error(std::string("batched apply: cudaMalloc(") + std::to_string(bytes) + ") failed: " + cudaGetErrorString(e));
-    return PHIKRON_ENOMEM;
-  }
+  PK_RET(device_malloc(p, bytes ? bytes : 16, "phikron_batch_create"));
   B.work.push_back(*p);
   B.work_bytes += bytes;
   return PHIKRON_OK;
@@ -69,7 +64,7 @@ int phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* 
     return PHIKRON_EINVAL;
   }
   *out = nullptr;
-  std::unique_ptr<phikron_batch_s> B(new (std::nothrow) phikron_batch_s());
+  std::unique_ptr<phikron_batch_s> B(alloc_fault() ? nullptr : new (std::nothrow) phikron_batch_s());
   if (!B) {
     set_error("phikron_batch_create: host allocation failed");
     return PHIKRON_ENOMEM;
@@ -167,6 +162,7 @@ int phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* 
             c.graph = true;
             c.ws = var >= 1;
             c.db = var == 2;
+            c.fuse = fused_weights_default();
             cfgs.push_back(c);
             if (!autotune) break;
           }

@@ -12,7 +12,7 @@ namespace phikron {
 
 struct Plan;
 
-enum StepKind { STEP_MODE = 0, STEP_WEIGHTED = 1, STEP_SQUARING = 2, STEP_EXPSCAN = 3 };
+enum StepKind { STEP_MODE = 0, STEP_WEIGHTED = 1, STEP_SQUARING = 2, STEP_EXPSCAN = 3, STEP_FUSED = 4 };
 
 struct Step {
   int kind;
@@ -27,6 +27,9 @@ struct Seq {
   std::vector<Step> steps;
   GJob* dG = nullptr;
   EJob* dE = nullptr;
+  FJob* dF = nullptr;      // fused node passes: jobs and their nodes
+  FNode* dFN = nullptr;
+  bool fused = false;      // the node phase ends in a fused weighted pass
   int* dSlots = nullptr;
   int nslots = 0;
   void** dPtrtab = nullptr;
@@ -56,6 +59,7 @@ struct SeqConfig {
   bool graph = true;      // capture the sequence as a CUDA graph
   bool ws = true;         // warp-specialised mode kernel
   bool db = false;        // double-buffered 128 x 64-tile mode kernel where every n >= 64
+  bool fuse = true;       // fold Algorithm 1's weights into the last node pass where it applies
 };
 
 struct MixedView {
@@ -72,6 +76,9 @@ struct MixedView {
 // contracted size is at least 64; "classic": the single-role kernel).
 bool mode_kernel_ws_default();
 bool mode_kernel_db_default();
+// Fused node-weight pass where it applies if the environment variable PHIKRON_FUSED_WEIGHTS is
+// "1" (measured slower than the separate passes on the 128^3 workload; see fused.cu).
+bool fused_weights_default();
 
 const MixedView mixed_view(const Plan& P, int d);
 int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& cfg);

@@ -40,6 +40,19 @@ void clear_error();
     if (r_ != PHIKRON_OK) return r_;                                                       \
   } while (0)
 
+// ----------------------------------------------------------------------------- allocation
+// Every device buffer of plans, sequences, batches and integrators comes from device_malloc,
+// and every library object from a host allocation that first asks alloc_fault(): both fail
+// with PHIKRON_ENOMEM (and a message naming `who`) when the allocation is refused.  Fault
+// injection for tests of the failure paths: with the environment variable
+// PHIKRON_FAIL_ALLOC_AFTER = k set, the library's allocations after the first k (counted from
+// the moment the variable took that value) are refused.
+bool alloc_fault();
+int device_malloc(void** p, size_t bytes, const char* who);
+// Frees a buffer from device_malloc (null is ignored); the library's count of live device
+// buffers (phikron_live_device_buffers) follows both.
+void device_free(void* p);
+
 // true if the address ranges [a, a + n) and [b, b + n) of n float64 share an element
 inline bool ranges_overlap(const void* a, const void* b, long long n) {
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);

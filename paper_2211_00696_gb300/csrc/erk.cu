@@ -111,14 +111,10 @@ struct phikron_erk_s {
   double *Au = nullptr, *D1 = nullptr, *D2 = nullptr, *D3 = nullptr, *U2 = nullptr, *V2 = nullptr, *Out = nullptr;
   ~phikron_erk_s() {
     for (phikron_plan_t p : plans) phikron_destroy(p);
-    for (void* a : allocs) cudaFree(a);
+    for (void* a : allocs) device_free(a);
   }
   int alloc(void** p, size_t bytes) {
-    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("phikron_erk_create: device allocation failed");
-      return PHIKRON_ENOMEM;
-    }
+    PK_RET(device_malloc(p, std::max<size_t>(bytes, 16), "phikron_erk_create"));
     allocs.push_back(*p);
     return PHIKRON_OK;
   }
@@ -213,7 +209,7 @@ int phikron_erk_create(phikron_erk_t* out, int method, int dims, const double* c
   phikron_opts_default(&o);
   if (opts) o = *opts;
   if (o.half_step) { set_error("phikron_erk_create: half_step is not used by the drivers"); return PHIKRON_EINVAL; }
-  phikron_erk_s* E = new (std::nothrow) phikron_erk_s();
+  phikron_erk_s* E = alloc_fault() ? nullptr : new (std::nothrow) phikron_erk_s();
   if (!E) { set_error("phikron_erk_create: host allocation failed"); return PHIKRON_ENOMEM; }
   E->method = method;
   E->dims = dims;

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <cmath>
 #include <vector>
 
@@ -19,6 +20,7 @@
 #include "plan.h"
 #include "profile.h"
 #include "batch.h"
+#include "ff_arith.cuh"
 
 namespace phikron {
 
@@ -27,76 +29,9 @@ namespace {
 constexpr int KC = 32;
 constexpr int SLICE_BYTES = 128 * KC * 2;
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
+using ff::to_f64;
 
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  e = b - (s - a);
-}
-
-// acc += c * t  in float-float
-__device__ __forceinline__ void ff_fma(float2& acc, float2 c, float2 t) {
-  const float p = c.x * t.x;
-  float pe = fmaf(c.x, t.x, -p);
-  pe = fmaf(c.x, t.y, pe);
-  pe = fmaf(c.y, t.x, pe);
-  float s, e;
-  two_sum(acc.x, p, s, e);
-  e += acc.y + pe;
-  fast_two_sum(s, e, acc.x, acc.y);
-}
-
-// acc += t
-__device__ __forceinline__ void ff_add(float2& acc, float2 t) {
-  float s, e;
-  two_sum(acc.x, t.x, s, e);
-  e += acc.y + t.y;
-  fast_two_sum(s, e, acc.x, acc.y);
-}
-
-// float-float -> float64 by integer assembly of the 53-bit significand (no float64 ops).
-// Requires |lo| <= ulp(hi)/2 (normalised pair).
-__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
-  const uint32_t bh = __float_as_uint(hi);
-  const int eh = (int)((bh >> 23) & 0xFF);
-  if (eh == 0) return 0.0;
-  uint64_t M = (uint64_t)((bh & 0x7FFFFFu) | 0x800000u) << 29;  // 53-bit significand of hi
-  int E = eh - 127 + 1023;
-  const uint32_t bl = __float_as_uint(lo);
-  const int el = (int)((bl >> 23) & 0xFF);
-  if (el != 0) {
-    const uint64_t ml = (uint64_t)((bl & 0x7FFFFFu) | 0x800000u);
-    const int sh = el - eh + 29;  // lo in units of hi's 53-bit ulp
-    uint64_t L;
-    if (sh >= 0)
-      L = ml << sh;
-    else if (sh > -40)
-      L = (ml + (1ull << (-sh - 1))) >> (-sh);
-    else
-      L = 0;
-    if (((bh ^ bl) >> 31) == 0) {
-      M += L;
-      if (M >> 53) {  // carry (cannot happen for normalised pairs; kept for safety)
-        M >>= 1;
-        ++E;
-      }
-    } else {
-      M -= L;
-      while (M && !(M >> 52)) {
-        M <<= 1;
-        --E;
-      }
-    }
-  }
-  const uint64_t bits = ((uint64_t)(bh >> 31) << 63) | ((uint64_t)E << 52) | (M & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)bits);
-}
-
-constexpr int MAXP = 8;
+constexpr int MAXP = 20;   // l_max of the mixed path (the paper's range, Sec. 4)
 constexpr int MAXM = 64;
 constexpr int EW_THREADS = 256;
 constexpr int EW_PAIRS = 4;  // element pairs per thread (vectors are float2 arrays of even length)
@@ -132,15 +67,15 @@ __device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
 __device__ __forceinline__ void st_pair(void* out, void* out2, bool f64, long long off, float2 a, float2 b, int& emax) {
   if (f64) {
     double* o = reinterpret_cast<double*>(out) + off;
-    o[0] = ff_to_f64(a.x, a.y);
-    o[1] = ff_to_f64(b.x, b.y);
+    o[0] = to_f64(a.x, a.y);
+    o[1] = to_f64(b.x, b.y);
   } else {
     *reinterpret_cast<float4*>(reinterpret_cast<float2*>(out) + off) = make_float4(a.x, a.y, b.x, b.y);
   }
   if (out2) {
     double* o = reinterpret_cast<double*>(out2) + off;
-    o[0] = ff_to_f64(a.x, a.y);
-    o[1] = ff_to_f64(b.x, b.y);
+    o[0] = to_f64(a.x, a.y);
+    o[1] = to_f64(b.x, b.y);
   }
   emax = max(emax, (int)((__float_as_uint(a.x) >> 23) & 0xFFu));
   emax = max(emax, (int)((__float_as_uint(b.x) >> 23) & 0xFFu));
@@ -179,10 +114,9 @@ __device__ __forceinline__ void block_exp_flush(int (&emax)[P_], int* out_exp, i
 // The T_k of a pair are read in batches (KB) before any arithmetic, so that each thread keeps
 // KB x 16 bytes of loads in flight.
 template <int P_>
-__global__ void __launch_bounds__(EW_THREADS, P_ <= 3 ? 4 : 3) g_weighted_kernel(const EJob* __restrict__ jobs,
-                                                                                 int njobs, long long total,
-                                                                                 const void* const* ptrtab) {
-  constexpr int KB = P_ <= 3 ? 6 : 4;  // T_k per batch (register budget without spills)
+__global__ void __launch_bounds__(EW_THREADS, P_ <= 3 ? 4 : (P_ <= 7 ? 3 : (P_ <= 11 ? 2 : 1)))
+    g_weighted_kernel(const EJob* __restrict__ jobs, int njobs, long long total, const void* const* ptrtab) {
+  constexpr int KB = P_ <= 3 ? 6 : (P_ <= 8 ? 4 : 2);  // T_k per batch (register budget without spills)
   __shared__ float2 cs[P_ * MAXM];
   __shared__ int red[P_][EW_THREADS / 32];
   int emax[P_];
@@ -222,8 +156,8 @@ __global__ void __launch_bounds__(EW_THREADS, P_ <= 3 ? 4 : 3) g_weighted_kernel
             if (k0 + q < m) {
 #pragma unroll
               for (int j = 0; j < P_; ++j) {
-                ff_fma(acc0[j], cs[j * m + k0 + q], t0[q]);
-                ff_fma(acc1[j], cs[j * m + k0 + q], t1[q]);
+                ff::fma_ff(acc0[j], cs[j * m + k0 + q], t0[q]);
+                ff::fma_ff(acc1[j], cs[j * m + k0 + q], t1[q]);
               }
             }
           }
@@ -238,7 +172,7 @@ __global__ void __launch_bounds__(EW_THREADS, P_ <= 3 ? 4 : 3) g_weighted_kernel
 
 // y-hat_i = 2^{-i}(Z_i + sum_{j<=i} y_j/(i-j)!), i = 1..p (Eq. (29)), grouped over jobs
 template <int P_>
-__global__ void __launch_bounds__(EW_THREADS, 4) g_squaring_kernel(const EJob* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(EW_THREADS, P_ <= 6 ? 4 : (P_ <= 11 ? 2 : 1)) g_squaring_kernel(const EJob* __restrict__ jobs, int njobs,
                                                                    long long total, const void* const* ptrtab,
                                                                    InvFact inv) {
   __shared__ int red[P_][EW_THREADS / 32];
@@ -277,11 +211,11 @@ __global__ void __launch_bounds__(EW_THREADS, 4) g_squaring_kernel(const EJob* _
           for (int j = 1; j <= q; ++j) {
             const int d = q - j;
             if (d <= 1) {
-              ff_add(a0, y0[j - 1]);
-              ff_add(a1, y1[j - 1]);
+              ff::add_ff(a0, y0[j - 1]);
+              ff::add_ff(a1, y1[j - 1]);
             } else {
-              ff_fma(a0, inv.f[d], y0[j - 1]);
-              ff_fma(a1, inv.f[d], y1[j - 1]);
+              ff::fma_ff(a0, inv.f[d], y0[j - 1]);
+              ff::fma_ff(a1, inv.f[d], y1[j - 1]);
             }
           }
           z0[q - 1] = make_float2(a0.x * sc, a0.y * sc);
@@ -381,7 +315,19 @@ int launch_ew_p(int kind, int p, const EJob* jobs, int njobs, long long blocks, 
     case 6: return launch_ew<6>(kind, jobs, njobs, blocks, tab, st);
     case 7: return launch_ew<7>(kind, jobs, njobs, blocks, tab, st);
     case 8: return launch_ew<8>(kind, jobs, njobs, blocks, tab, st);
-    default: set_error("mixed path: l_max must be in 1..8"); return PHIKRON_ENOTSUP;
+    case 9: return launch_ew<9>(kind, jobs, njobs, blocks, tab, st);
+    case 10: return launch_ew<10>(kind, jobs, njobs, blocks, tab, st);
+    case 11: return launch_ew<11>(kind, jobs, njobs, blocks, tab, st);
+    case 12: return launch_ew<12>(kind, jobs, njobs, blocks, tab, st);
+    case 13: return launch_ew<13>(kind, jobs, njobs, blocks, tab, st);
+    case 14: return launch_ew<14>(kind, jobs, njobs, blocks, tab, st);
+    case 15: return launch_ew<15>(kind, jobs, njobs, blocks, tab, st);
+    case 16: return launch_ew<16>(kind, jobs, njobs, blocks, tab, st);
+    case 17: return launch_ew<17>(kind, jobs, njobs, blocks, tab, st);
+    case 18: return launch_ew<18>(kind, jobs, njobs, blocks, tab, st);
+    case 19: return launch_ew<19>(kind, jobs, njobs, blocks, tab, st);
+    case 20: return launch_ew<20>(kind, jobs, njobs, blocks, tab, st);
+    default: set_error("mixed path: l_max must be in 1..20"); return PHIKRON_ENOTSUP;
   }
 }
 
@@ -474,10 +420,14 @@ int precision_setup(Plan& P) {
     }
   }
   if (P.p > MAXP || P.m > MAXM) {
-    set_error("mixed path: needs l_max <= 8 and at most 64 quadrature nodes");
+    set_error("mixed path: needs l_max <= 20 and at most 64 quadrature nodes");
     return PHIKRON_ENOTSUP;
   }
-  MixedState* M = new MixedState();
+  MixedState* M = alloc_fault() ? nullptr : new (std::nothrow) MixedState();
+  if (!M) {
+    set_error("mixed plan state: host allocation failed");
+    return PHIKRON_ENOMEM;
+  }
   P.mixed = M;
   P.mixed_free = mixed_free;
   int slices = P.opts.slices;
@@ -540,6 +490,7 @@ int precision_setup(Plan& P) {
   cfg.graph = true;
   cfg.ws = mode_kernel_ws_default();
   cfg.db = mode_kernel_db_default();
+  cfg.fuse = fused_weights_default();
   PK_RET(seq_build(M->seq, units, 1, cfg));
   return PHIKRON_OK;
 }
@@ -555,6 +506,8 @@ int apply_mixed(Plan& P, const double* V, double* Out, cudaStream_t st) {
 
 int mixed_slices(const Plan& P) { return static_cast<const MixedState*>(P.mixed)->slices; }
 
+bool mixed_fused(const Plan& P) { return P.mixed && static_cast<const MixedState*>(P.mixed)->seq.fused; }
+
 int mixed_status(Plan& P, int* status) {
   if (!P.mixed) {
     *status = 0;
@@ -568,19 +521,14 @@ int mixed_status(Plan& P, int* status) {
 
 Seq::~Seq() {
   if (exec) cudaGraphExecDestroy(exec);
-  for (void* p : allocs) cudaFree(p);
+  for (void* p : allocs) device_free(p);
 }
 
 namespace {
 
 int seq_alloc(Seq& S, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  const cudaError_t e = cudaMalloc(p, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
-    return PHIKRON_ENOMEM;
-  }
+  PK_RET(device_malloc(p, bytes, "launch sequence"));
   S.allocs.push_back(*p);
   S.device_bytes += bytes;
   return PHIKRON_OK;
@@ -594,6 +542,8 @@ long long job_tiles(const GJob& j, const PassShape& s) {
 struct Builder {
   std::vector<GJob> gjobs;
   std::vector<EJob> ejobs;
+  std::vector<FJob> fjobs;
+  std::vector<FNode> fnodes;
   std::vector<Step> steps;
   int nslots = 0;
   bool big_first = false;
@@ -616,6 +566,28 @@ struct Builder {
     s.total = t;
     s.shape = shape;
     gjobs.insert(gjobs.end(), jobs.begin(), jobs.end());
+    steps.push_back(s);
+  }
+
+  // jobs[u].node0 indexes `nodes`; both are appended to the builder's tables
+  void fused_step(std::vector<FJob> jobs, const std::vector<FNode>& nodes, const PassShape& shape, int p) {
+    if (jobs.empty()) return;
+    long long t = 0;
+    const int base = (int)fnodes.size();
+    for (FJob& j : jobs) {
+      j.tile_begin = t;
+      t += (j.B0 + fused::kFibers - 1) / fused::kFibers;
+      j.node0 += base;
+    }
+    Step s{};
+    s.kind = STEP_FUSED;
+    s.off = fjobs.size();
+    s.count = (int)jobs.size();
+    s.total = t;
+    s.p = p;
+    s.shape = shape;
+    fjobs.insert(fjobs.end(), jobs.begin(), jobs.end());
+    fnodes.insert(fnodes.end(), nodes.begin(), nodes.end());
     steps.push_back(s);
   }
 
@@ -651,6 +623,11 @@ bool mode_kernel_ws_default() {
 bool mode_kernel_db_default() {
   const char* v = std::getenv("PHIKRON_MODE_KERNEL");
   return v && std::strcmp(v, "db") == 0;
+}
+
+bool fused_weights_default() {
+  const char* v = std::getenv("PHIKRON_FUSED_WEIGHTS");
+  return v && std::strcmp(v, "1") == 0;
 }
 
 int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& cfg) {
@@ -741,10 +718,12 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
     bool out_f64;
     int out_slot;          // -1 none
   };
-  auto chain = [&](const std::vector<CV>& vs, bool first_f64) -> int {
+  // passes d < npass of the chain (all when npass = dims); cur_out receives the exponent slot
+  // of every vector after the last pass run
+  auto chain = [&](const std::vector<CV>& vs, bool first_f64, int npass, std::vector<int>* cur_out) -> int {
     std::vector<int> cur(vs.size());
     for (size_t q = 0; q < vs.size(); ++q) cur[q] = vs[q].in_slot;
-    for (int d = 0; d < dims; ++d) {
+    for (int d = 0; d < npass; ++d) {
       const bool last = (d == dims - 1);
       std::vector<GJob> jobs;
       std::vector<int> newslot(vs.size(), -1);
@@ -814,10 +793,18 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       for (size_t q = 0; q < vs.size(); ++q)
         if (newslot[q] >= 0) cur[q] = newslot[q];
     }
+    if (cur_out) *cur_out = cur;
     return PHIKRON_OK;
   };
 
-  // 2. node phase: m node actions (to T), phi_0 (to Out[0]), half-step phi_0 (to Out[p+1])
+  // 2. node phase: m node actions (to T), phi_0 (to Out[0]), half-step phi_0 (to Out[p+1]).
+  // Fused: the last pass of the chain runs as one fused pass that folds Algorithm 1's weights
+  // into its epilogue (fused.cu) and writes y_1..y_p itself; needs a float-float last pass (dims
+  // >= 2) over a factor of at most FW_MAXN rows and 1 <= p <= FW_MAXP.
+  bool fuse = cfg.fuse && p >= 1 && p <= FW_MAXP && dims >= 2;
+  for (int u = 0; u < nu && fuse; ++u)
+    if (units[u].plan->n[dims - 1] > FW_MAXN) fuse = false;
+  S.fused = fuse;
   std::vector<float2*> T(nu);
   std::vector<int> tslot(nu);
   {
@@ -835,12 +822,74 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
         vs.push_back(CV{u, P.m + P.s, nullptr, us[u].vslot, true, P.m + 1, nullptr, true,
                         (long long)(p + 1) * P.N * 8, true, -1});
     }
-    PK_RET(chain(vs, true));
+    if (!fuse) {
+      PK_RET(chain(vs, true, dims, nullptr));
+    } else {
+      std::vector<int> cur;
+      PK_RET(chain(vs, true, dims - 1, &cur));
+      // the fused last pass: one job per unit over its nodes (weighted first, then direct)
+      std::vector<FJob> fj;
+      std::vector<FNode> fn;
+      size_t q = 0;
+      const int dl = dims - 1;
+      for (int u = 0; u < nu; ++u) {
+        const Plan& P = *units[u].plan;
+        const MixedView mv = mixed_view(P, dl);
+        const float2* src = (dl % 2 == 1) ? units[u].W1 : units[u].W2;   // written by pass dl - 1
+        FJob j{};
+        j.n = P.n[dl];
+        j.B0 = P.N / P.n[dl];
+        j.node0 = (int)fn.size();
+        j.m = P.m;
+        j.coef = mv.coef;
+        j.stride = P.N;
+        j.out_tab = j.out2_tab = -1;
+        if (P.s == 0) {
+          j.out_tab = 2 * units[u].inst + 1;
+          j.tab_off_out = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)P.N * 8;
+          j.out_f64 = 1;
+        } else {
+          j.out = us[u].Y;
+          us[u].yslot = us[u].next;
+          us[u].next += p;
+          j.out_exp = slots + us[u].yslot;
+        }
+        if (cfg.half && P.s == 1) {
+          j.out2_tab = 2 * units[u].inst + 1;
+          j.tab_off_out2 = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)(p + 2) * P.N * 8;
+        }
+        // the vectors of this unit in vs are contiguous, in the order pushed above
+        for (; q < vs.size() && vs[q].u == u; ++q) {
+          const CV& c = vs[q];
+          FNode nd{};
+          nd.in = src + (size_t)c.vec * P.N;
+          nd.in_exp = slots + cur[q];
+          nd.eslices = mv.sl + mv.mat_bytes * (size_t)c.mat;
+          nd.rexp = mv.rexp + (size_t)mv.rexp_stride * c.mat;
+          nd.out_tab = -1;
+          if (c.out_tab) {   // phi_0 (or phi_0 at tau/2): stored as it is, float64
+            nd.direct = 1;
+            nd.out_tab = 2 * units[u].inst + 1;
+            nd.tab_off_out = (long long)units[u].rhs * out_mult * P.N * 8 + c.out_off;
+          } else {
+            nd.direct = 0;
+            nd.k = c.mat;
+          }
+          fn.push_back(nd);
+        }
+        j.nnodes = (int)fn.size() - j.node0;
+        fj.push_back(j);
+      }
+      PassShape sh{};
+      sh.slices = cfg.slices;
+      sh.grid = cfg.grid;
+      B.fused_step(fj, fn, sh, p);
+    }
   }
   if (p >= 1) {
-    // 3. weighted sums
+    // 3. weighted sums (already written by the fused pass when it ran)
     std::vector<EJob> ej;
-    for (int u = 0; u < nu; ++u) {
+    for (int u = 0; u < nu && !fuse; ++u) {
       const Plan& P = *units[u].plan;
       const MixedView mv = mixed_view(P, 0);
       EJob j{};
@@ -882,7 +931,7 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
           vs.push_back(CV{u, P.m + 1 + t, us[u].Y + (size_t)i * P.N, us[u].yslot + i, false, i,
                           Z + (size_t)i * P.N, false, 0, false, -1});
       }
-      PK_RET(chain(vs, false));
+      PK_RET(chain(vs, false, dims, nullptr));
       std::vector<EJob> sj;
       for (int u : part) {
         const Plan& P = *units[u].plan;
@@ -925,6 +974,12 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
   // upload the job tables
   PK_RET(seq_alloc(S, (void**)&S.dG, sizeof(GJob) * std::max<size_t>(1, B.gjobs.size())));
   PK_RET(seq_alloc(S, (void**)&S.dE, sizeof(EJob) * std::max<size_t>(1, B.ejobs.size())));
+  PK_RET(seq_alloc(S, (void**)&S.dF, sizeof(FJob) * std::max<size_t>(1, B.fjobs.size())));
+  PK_RET(seq_alloc(S, (void**)&S.dFN, sizeof(FNode) * std::max<size_t>(1, B.fnodes.size())));
+  if (!B.fjobs.empty())
+    PK_TRY_CUDA(cudaMemcpy(S.dF, B.fjobs.data(), sizeof(FJob) * B.fjobs.size(), cudaMemcpyHostToDevice));
+  if (!B.fnodes.empty())
+    PK_TRY_CUDA(cudaMemcpy(S.dFN, B.fnodes.data(), sizeof(FNode) * B.fnodes.size(), cudaMemcpyHostToDevice));
   if (!B.gjobs.empty())
     PK_TRY_CUDA(cudaMemcpy(S.dG, B.gjobs.data(), sizeof(GJob) * B.gjobs.size(), cudaMemcpyHostToDevice));
   if (!B.ejobs.empty())
@@ -964,6 +1019,15 @@ int seq_launch_all(Seq& S, cudaStream_t st) {
       P.ptrtab = S.dPtrtab;
       P.wait_ns = S.wait_ns;
       PK_RET(tc::mode_pass(P, s.shape, S.dStatus, st));
+    } else if (s.kind == STEP_FUSED) {
+      FPass F;
+      F.jobs = S.dF + s.off;
+      F.nodes = S.dFN;
+      F.njobs = s.count;
+      F.total_tiles = s.total;
+      F.ptrtab = S.dPtrtab;
+      F.wait_ns = S.wait_ns;
+      PK_RET(fused::launch(F, s.shape.slices, s.p, s.shape.grid, S.dStatus, st));
     } else if (s.kind == STEP_EXPSCAN) {
       launch_begin(KC_CONVERT, st);
       g_expscan_kernel<<<ew_grid(g_expscan_kernel, s.total), EW_THREADS, 0, st>>>(S.dE + s.off, s.count, s.total,
@@ -985,7 +1049,7 @@ int seq_run(Seq& S, const PtrArgs& args, cudaStream_t st) {
     if (pr) {
       pr->launches += (long long)S.steps.size();
       for (const Step& s : S.steps)
-        pr->launches_by_class[s.kind == STEP_MODE ? KC_TC_MODE
+        pr->launches_by_class[(s.kind == STEP_MODE || s.kind == STEP_FUSED) ? KC_TC_MODE
                               : s.kind == STEP_WEIGHTED ? KC_WEIGHTED
                               : s.kind == STEP_SQUARING ? KC_SQUARING : KC_CONVERT]++;
     }

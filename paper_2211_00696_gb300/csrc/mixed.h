@@ -66,6 +66,59 @@ size_t smem_bytes(int ks, int sub);
 // fibers per tile of a pass: 64 for the double-buffered kernel, 128 otherwise
 inline long long tile_fibers(const PassShape& s) { return s.db ? 64 : 128; }
 
+// Fused last mode pass of the node phase (fused.cu): for every output tile the kernel runs the
+// last mode product of every node of its unit one after the other and folds the weighted ones
+// into the p sums y_j = sum_k c_{j,k} T_k of Algorithm 1 (Sec. 3.1) in TMEM, so that the node
+// products T_k never reach HBM; "direct" nodes (phi_0, and phi_0 at tau/2) are stored as they
+// are.  Contraction over the fastest axis (R = 1), float-float inputs, n <= 128, p <= 4.
+constexpr int FW_MAXP = 4;     // weighted outputs a fused pass holds in TMEM
+constexpr int FW_MAXN = 128;   // contracted size (one E row block)
+
+struct FNode {
+  const float2* in;        // the node's input vector (float-float)
+  const int* in_exp;       // e with |in| < 2^e
+  const uint8_t* eslices;  // E sliced as for GJob (n <= 128: one row block)
+  const int* rexp;         // the 128 row exponents of E
+  void* out;               // direct node: float64 output vector (or table entry + offset)
+  long long tab_off_out;
+  int out_tab;             // -1: `out` is a direct pointer
+  int direct;              // 1: store the product; 0: weighted node `k`
+  int k;
+  int pad_;
+};
+
+struct FJob {
+  long long B0;            // fibers (product of the slower axes)
+  long long tile_begin;    // first tile (32 fibers) of this job in its pass
+  int n;                   // contracted size (multiple of 16, <= FW_MAXN)
+  int node0, nnodes;       // nodes [node0, node0 + nnodes): the m weighted ones first
+  int m;                   // weighted nodes (columns of coef)
+  const float2* coef;      // p x m float-float weights, (j-1)*m + k
+  void* out;               // y_j at out + (j-1)*stride elements: float2, or float64 (out_f64)
+  void* out2;              // optional float64 copy of y_j (half-step outputs), or null
+  long long stride, tab_off_out, tab_off_out2;
+  int out_tab, out2_tab;   // pointer-table entries, or -1
+  int out_f64;
+  int pad_;
+  int* out_exp;            // p exponent slots (float2 outputs), or null
+};
+
+struct FPass {
+  const FJob* jobs;        // device array, sorted by tile_begin
+  const FNode* nodes;      // device array
+  int njobs;
+  long long total_tiles;
+  const void* const* ptrtab;
+  unsigned long long wait_ns;
+};
+
+namespace fused {
+// Runs one fused pass with `slices` digit slices and p weighted outputs on `grid` CTAs.
+int launch(const FPass& P, int slices, int p, int grid, int* status, cudaStream_t st);
+// Fibers per tile of a fused pass.
+constexpr int kFibers = 32;
+}  // namespace fused
+
 // Grouped float-float elementwise jobs (mixed.cu): weighted sums of Algorithm 1, modified
 // squaring of Eq. (29), and the exponent scan of a float64 input.
 struct EJob {

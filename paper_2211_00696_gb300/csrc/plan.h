@@ -82,6 +82,8 @@ int apply_mixed(Plan& P, const double* V, double* Out, cudaStream_t st);
 // Reads and clears the device status word of the mixed path (synchronous).
 int mixed_status(Plan& P, int* status);
 int mixed_slices(const Plan& P);
+// true if the plan's mixed apply folds Algorithm 1's weights into its last node pass
+bool mixed_fused(const Plan& P);
 // Prepares precision-specific plan state (no-op for FP64).
 int precision_setup(Plan& P);
 // Runs the apply for nrhs right-hand sides with the plan's precision.

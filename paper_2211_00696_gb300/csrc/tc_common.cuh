@@ -7,6 +7,7 @@
 
 #include <cstdint>
 
+#include "ff_arith.cuh"
 #include "mixed.h"
 
 namespace phikron {
@@ -251,41 +252,9 @@ __device__ __forceinline__ float pow2f_full(int e) {
 }
 
 // ---------------------------------------------------------------- float-float helpers
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  e = b - (s - a);
-}
-
-// float-float -> float64 by integer assembly of the 53-bit significand (no float64 ops);
-// requires |lo| <= ulp(hi)/2.
-__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
-  const uint32_t bh = __float_as_uint(hi);
-  const int eh = (int)((bh >> 23) & 0xFF);
-  if (eh == 0) return 0.0;
-  uint64_t M = (uint64_t)((bh & 0x7FFFFFu) | 0x800000u) << 29;
-  int E = eh - 127 + 1023;
-  const uint32_t bl = __float_as_uint(lo);
-  const int el = (int)((bl >> 23) & 0xFF);
-  if (el != 0) {
-    const uint64_t ml = (uint64_t)((bl & 0x7FFFFFu) | 0x800000u);
-    const int sh = el - eh + 29;
-    const uint64_t L = sh >= 0 ? (ml << sh) : (sh > -40 ? ((ml + (1ull << (-sh - 1))) >> (-sh)) : 0ull);
-    if (((bh ^ bl) >> 31) == 0) {
-      M += L;
-      if (M >> 53) { M >>= 1; ++E; }
-    } else {
-      M -= L;
-      while (M && !(M >> 52)) { M <<= 1; --E; }
-    }
-  }
-  return __longlong_as_double((long long)(((uint64_t)(bh >> 31) << 63) | ((uint64_t)E << 52) | (M & 0xFFFFFFFFFFFFFull)));
-}
+using ff::two_sum;
+using ff::fast_two_sum;
+__device__ __forceinline__ double ff_to_f64(float hi, float lo) { return ff::to_f64(hi, lo); }
 
 __device__ __forceinline__ float pow2f(int e) {
   e = e < -126 ? -126 : (e > 127 ? 127 : e);

@@ -44,7 +44,7 @@ class Info(C.Structure):
                 ("alpha", C.c_double), ("log10_bound", C.c_double), ("precision", C.c_int),
                 ("quad", C.c_int), ("selector_used", C.c_int), ("unique_factors", C.c_int),
                 ("device_bytes", C.c_size_t), ("slices", C.c_int), ("adaptive_nodes", C.c_int),
-                ("adaptive_err", C.c_double)]
+                ("adaptive_err", C.c_double), ("fused_weights", C.c_int)]
 
 
 class Profile(C.Structure):
@@ -118,6 +118,7 @@ SIGNATURES = {
     "phikron_gauss_legendre": (C.c_int, [C.c_int, _DP, _DP]),
     "phikron_clenshaw_curtis": (C.c_int, [C.c_int, _DP, _DP]),
     "phikron_expm_workspace_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "phikron_live_device_buffers": (C.c_longlong, []),
     "phikron_expm_batched": (C.c_int, [C.c_int, C.c_int, C.c_void_p, _DP, _DP, C.c_void_p,
                                        C.c_void_p, C.c_void_p]),
     "phikron_kron_apply_f64": (C.c_int, [C.c_int, _IP, C.POINTER(C.c_void_p), C.c_void_p,
