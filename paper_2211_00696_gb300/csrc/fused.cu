@@ -19,17 +19,19 @@
 // brought into shared memory by one bulk copy (cp.async.bulk) that the scheduler thread issues
 // ahead into a ring of raw buffers; the producer warps cut it into digit slices chunk by chunk
 // (32 K values), next to the chunk's E slices (one bulk copy each).  Roles (15 warps):
-//   warps 0-7   producers: digit slices of X; thread 0 also starts each chunk's E copy
-//   warps 8-11  epilogue: warp 8+q owns TMEM lanes 32q..32q+31 (= rows i of E)
+//   warps 0-3   producers: digit slices of X; thread 0 also starts each chunk's E copy
+//   warps 4-11  epilogue: warp w owns TMEM lanes 32 (w % 4) .. + 31 (= rows i of E) and the
+//               columns (fibers) 16 h .. 16 h + 15, h = (w - 4) / 4 (two warps per lane quarter)
 //   warps 12,14 lane 0 issues the MMAs of accumulators {0, 3} resp. {1, 2}
 //   warp 13     lane 0: per (tile, node) context into a 4-slot ring, and the raw X copies
 // Every mbarrier wait is bounded (FPass::wait_ns); on expiry the CTA records PHIKRON_ETIMEOUT,
 // every role stops at its next check, and the CTA waits for its own bulk copies and MMAs before
 // it releases TMEM.
 //
-// Opt-in (PHIKRON_FUSED_WEIGHTS=1): on the 128^3 convection-diffusion workload (11 node vectors,
-// 4 digit slices) this pass took ~0.41 ms against ~0.10 ms for the separate last mode pass plus
-// 0.06 ms for the weighted sums.
+// Per (tile, node) step the slice MMAs (80 of N = 32 at 4 digit slices) take ~2.7 us, which
+// bounds the pass; the write-out of y_j and of the direct products comes on top once per tile.
+// On the 128^3 convection-diffusion workload (11 node vectors, 4 digit slices) the pass takes
+// ~0.15 ms against ~0.10 + 0.06 ms for the separate last mode pass and weighted sums.
 #include <algorithm>
 #include <cstdint>
 
@@ -45,8 +47,8 @@ namespace {
 constexpr int FW_FIB = fused::kFibers;         // fibers per tile (MMA N)
 constexpr int FW_XSL = FW_FIB * KC * 2;        // one X slice of a chunk: 32 rows x 64 B
 constexpr int FW_RAW = FW_FIB * FW_MAXN * 8;   // raw float-float X of a (tile, node): 32 KB
-constexpr int FW_EPI0 = 8, FW_MMA = 12, FW_SCHED = 13, FW_MMA2 = 14;
-constexpr int FW_THREADS = 480, FW_PROD = 256, FW_EPI = 128, FW_ISSUERS = 2, FW_SLOTS = 4;
+constexpr int FW_EPI0 = 4, FW_MMA = 12, FW_SCHED = 13, FW_MMA2 = 14;
+constexpr int FW_THREADS = 480, FW_PROD = 128, FW_EPI = 256, FW_ISSUERS = 2, FW_SLOTS = 4;
 constexpr int FW_SLOT_READERS = FW_PROD + FW_ISSUERS + FW_EPI;
 constexpr int FW_MASK1 = 0b1001, FW_MASK2 = 0b0110;
 constexpr int FW_BAR_BYTES = 256, FW_SLOT_BYTES = 512;
@@ -78,12 +80,34 @@ struct FwSlot {
 };
 static_assert(sizeof(FwSlot) * FW_SLOTS <= FW_SLOT_BYTES, "slot ring");
 
+// all 256 epilogue threads (named barrier 1): true if any of them passes true
+__device__ __forceinline__ bool epi_vote_any256(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, 1, 256, q;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return r != 0;
+}
+
+// one arrival of count 32 for the whole (converged) warp instead of 32 arrivals on one word
+__device__ __forceinline__ void mbar_arrive_warp(uint32_t mbar, int lane) {
+  __syncwarp();
+  if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], 32;" ::"r"(mbar) : "memory");
+}
+
+// reads slot sc once it is filled, then releases it: lane >= 0 for a whole warp (one arrival
+// of count 32), lane < 0 for a single thread
 __device__ __forceinline__ bool fw_get(const FwSlot* slots, uint64_t* slot_full, uint64_t* slot_empty, uint32_t sc,
-                                       FwSlot& out, unsigned long long wl) {
+                                       FwSlot& out, unsigned long long wl, int lane) {
   const uint32_t q = sc % FW_SLOTS;
   const bool ok = mbar_wait(smem_u32(&slot_full[q]), (sc / FW_SLOTS) & 1u, wl);
   if (ok) out = slots[q];
-  mbar_arrive(smem_u32(&slot_empty[q]));
+  if (lane >= 0)
+    mbar_arrive_warp(smem_u32(&slot_empty[q]), lane);
+  else
+    mbar_arrive(smem_u32(&slot_empty[q]));
   return ok;
 }
 
@@ -98,7 +122,68 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
       : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Writes this warp's column half ch of nvec float-float vectors of a tile from TMEM (hi at
+// sums + 64 v, lo 32 columns further, column = fiber) to y + v * stride + col * n + i: float-float (yff), float64 (y64) and/or a
+// float64 copy (y2); with out_exp, the exponent of each vector's largest |hi| goes to
+// out_exp[v].  It runs once or twice per tile, so its loops stay rolled: fully unrolled copies
+// of it in the node loop cost instruction-cache misses on every tile.  Called by every lane of
+// an epilogue warp.
+__device__ __forceinline__ void fw_write_out(uint32_t sums, int nvec, int ch, bool vi, int i, int lane, int n, int nfib,
+                                          long long stride, float2* yff, double* y64, double* y2, int* out_exp) {
+#pragma unroll 1
+  for (int v = 0; v < nvec; ++v) {
+    uint32_t mx = 0;
+#pragma unroll 1
+    for (int g = 2 * ch; g < 2 * ch + 2; ++g) {   // this warp's half, 8 columns at a time
+      float h[8], l[8];
+      tmem_ld8(sums + 64u * v + 8u * g, h);
+      tmem_ld8(sums + 64u * v + 32u + 8u * g, l);
+      tmem_wait_ld();
+      if (vi) {
+        const long long o = (long long)v * stride + (long long)(8 * g) * n + i;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (8 * g + q < nfib) {
+            const long long e = o + (long long)q * n;
+            if (yff) yff[e] = make_float2(h[q], l[q]);
+            if (y64 || y2) {
+              const double d = ff::to_f64(h[q], l[q]);
+              if (y64) y64[e] = d;
+              if (y2) y2[e] = d;
+            }
+            mx = max(mx, __float_as_uint(h[q]) & 0x7FFFFFFFu);
+          }
+        }
+      }
+    }
+    if (out_exp) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      // |y| < 2^{biased - 126}; a zero output keeps the slot's initial (very negative) value
+      const int emax = (int)(mx >> 23);
+      if (lane == 0 && emax > 0) atomicMax(out_exp + v, emax - 126);
+    }
+  }
+}
 
 template <int KS, int P_>
 __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __grid_constant__ FPass P, int* status) {
@@ -161,8 +246,8 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
 
   if (warp < FW_EPI0) {
     // ------------------------------------------------------------ producers
-    const int f = tid >> 3;    // fiber of the tile
-    const int kq = tid & 7;    // K values 4 kq .. 4 kq + 3 of every 32-wide chunk
+    const int f = tid >> 2;    // fiber of the tile
+    const int kq = tid & 3;    // K values 8 kq .. 8 kq + 7 of every 32-wide chunk
     uint32_t sc = 0, it = 0;
     int e_last = -1;           // thread 0: chunk of the latest E bulk copy
     bool stop = false;
@@ -170,10 +255,10 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
       while (true) {
         FwSlot S;
         const uint32_t r = sc % NRAW;
-        if (!fw_get(slots, slot_full, slot_empty, sc, S, wl) ||
+        if (!fw_get(slots, slot_full, slot_empty, sc, S, wl, lane) ||
             !mbar_wait(smem_u32(&raw_full[r]), (sc / NRAW) & 1u, wl))
           ws_fail(abort_s, status);
-        if (*abort_s) { stop = true; break; }
+        if (__any_sync(0xffffffffu, *abort_s)) { stop = true; break; }   // warp-uniform
         const float xsc = pow2f_full(-S.eX);
         const float2* raw = reinterpret_cast<const float2*>(rawbuf + r * FW_RAW) + (long long)f * S.n;
         const bool vf = f < S.nfib;
@@ -181,32 +266,38 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
           const uint32_t st = it % NST, use = it / NST;
           uint8_t* sX = smem + st * STAGE;
           if (use >= 1 && !mbar_wait(smem_u32(&empty[st]), (use - 1) & 1u, wl)) ws_fail(abort_s, status);
-          if (*abort_s) { stop = true; break; }
+          if (__any_sync(0xffffffffu, *abort_s)) { stop = true; break; }
           if (tid == 0) {
             e_last = (int)it;
             mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)(KS * SLICE_BYTES));
             bulk_copy_g2s(smem_u32(sX + XBYTES), S.ebase + (size_t)c * KS * SLICE_BYTES, (uint32_t)(KS * SLICE_BYTES),
                           smem_u32(&full_e[st]));
           }
-          const int k0 = c * KC + 4 * kq;
-          float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-          if (vf && k0 < S.n) {  // n is a multiple of 16: k0 < n covers k0 .. k0 + 3
-            v0 = *reinterpret_cast<const float4*>(raw + k0);
-            v1 = *reinterpret_cast<const float4*>(raw + k0 + 2);
+          const int k0 = c * KC + 8 * kq;
+          float4 v[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (vf && k0 < S.n) {  // n is a multiple of 16: k0 < n covers k0 .. k0 + 7
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = *reinterpret_cast<const float4*>(raw + k0 + 2 * e);
           }
-          float2 a[KS], b[KS];
-          cut_ff_float2<KS>(make_float2(v0.x, v0.z), make_float2(v0.y, v0.w), xsc, a);
-          cut_ff_float2<KS>(make_float2(v1.x, v1.z), make_float2(v1.y, v1.w), xsc, b);
-          const uint32_t off = chunk_offset(f, kq >> 1) + (kq & 1) * 8;
+          uint32_t pk[KS][4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float2 a[KS];
+            cut_ff_float2<KS>(make_float2(v[e].x, v[e].z), make_float2(v[e].y, v[e].w), xsc, a);
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl) pk[sl][e] = pack_bf16x2(a[sl].x, a[sl].y);
+          }
+          const uint32_t off = chunk_offset(f, kq);
 #pragma unroll
           for (int sl = 0; sl < KS; ++sl)
-            *reinterpret_cast<uint2*>(sX + sl * FW_XSL + off) =
-                make_uint2(pack_bf16x2(a[sl].x, a[sl].y), pack_bf16x2(b[sl].x, b[sl].y));
+            *reinterpret_cast<uint4*>(sX + sl * FW_XSL + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(smem_u32(&full_x[st]));
+          mbar_arrive_warp(smem_u32(&full_x[st]), lane);
         }
         if (stop) break;
-        mbar_arrive(smem_u32(&raw_empty[r]));   // this thread is done with the raw X of step sc
+        mbar_arrive_warp(smem_u32(&raw_empty[r]), lane);   // this warp is done with the raw X of step sc
         ++sc;
         if (S.flags & FW_END) break;
       }
@@ -218,56 +309,47 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
     }
   } else if (warp < FW_MMA) {
     // ------------------------------------------------------------ epilogue
-    const int i = tid - FW_EPI0 * 32;   // TMEM lane = row i of E = output index along the fastest axis
-    const uint32_t lane_base = tmem + ((uint32_t)((i >> 5) * 32) << 16);
+    const int i = (warp & 3) * 32 + lane;         // TMEM lane = row i of E = output index along the fastest axis
+    const int ch = (warp - FW_EPI0) >> 2;         // column half: fibers 16 ch .. 16 ch + 15
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t sc = 0;
     bool stop = false;
     for (long long tile = blockIdx.x; tile < total_tiles && !stop; tile += gridDim.x) {
       while (true) {
         FwSlot S;
         const uint32_t b = sc & 1u;
-        bool ok = fw_get(slots, slot_full, slot_empty, sc, S, wl);
+        bool ok = fw_get(slots, slot_full, slot_empty, sc, S, wl, lane);
         ok = ok && mbar_wait(smem_u32(&tmem_full[b]), (sc >> 1) & 1u, wl);
         if (!ok) ws_fail(abort_s, status);
-        if (epi_vote_any(!ok || *abort_s)) { stop = true; break; }
+        if (epi_vote_any256(!ok || *abort_s)) { stop = true; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const bool vi = i < S.n;
         const float scl = pow2f(S.eX + (vi ? __ldg(S.rexp + i) : 0));
         const float2 sc2 = make_float2(scl, scl);
         const bool direct = (S.flags & FW_DIRECT) != 0;
-        const bool first = (S.flags & FW_FIRST) != 0, last = (S.flags & FW_LAST) != 0;
+        const bool first = (S.flags & FW_FIRST) != 0;
         const uint32_t lv = lane_base + 128u * b;
-        uint32_t mx[FW_MAXP] = {0u, 0u, 0u, 0u};
-        // outputs of the last weighted node
-        const FJob* J = &P.jobs[S.job];
-        float2* yff = nullptr;
-        double* y64 = nullptr;
-        double* y2 = nullptr;
-        if (last) {
-          void* o = J->out_tab >= 0 ? (void*)((char*)P.ptrtab[J->out_tab] + J->tab_off_out) : J->out;
-          if (J->out_f64) y64 = reinterpret_cast<double*>(o); else yff = reinterpret_cast<float2*>(o);
-          if (J->out2_tab >= 0 || J->out2)
-            y2 = reinterpret_cast<double*>(J->out2_tab >= 0 ? (void*)((char*)P.ptrtab[J->out2_tab] + J->tab_off_out2)
-                                                           : J->out2);
-        }
-        const long long ybase = (S.f0 * (long long)S.n) + i;
+        const uint32_t sums = lane_base + FW_SUMS;
+        // two groups of 8 columns (fibers) of this warp's half: a group's level values, T_k and
+        // sums stay in registers
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          const int cc = 16 * g;
-          float d2[16], d3[16], d4[16], d5[16];
-          tmem_ld16(lv + (uint32_t)cc, d2);
-          tmem_ld16(lv + 32u + (uint32_t)cc, d3);
-          tmem_ld16(lv + 64u + (uint32_t)cc, d4);
-          if (KS >= 4) tmem_ld16(lv + 96u + (uint32_t)cc, d5);
+        for (int gg = 0; gg < 2; ++gg) {
+          const int g = 2 * ch + gg;
+          const int cc = 8 * g;
+          float d2[8], d3[8], d4[8], d5[8];
+          tmem_ld8(lv + (uint32_t)cc, d2);
+          tmem_ld8(lv + 32u + (uint32_t)cc, d3);
+          tmem_ld8(lv + 64u + (uint32_t)cc, d4);
+          if (KS >= 4) tmem_ld8(lv + 96u + (uint32_t)cc, d5);
           tmem_wait_ld();
-          if (g == 1) {
-            // both column groups are in registers: the accumulators of buffer b are free
+          if (gg == 1) {
+            // this warp's column groups are in registers: its part of buffer b is free
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(smem_u32(&tmem_empty[b]));
+            mbar_arrive_warp(smem_u32(&tmem_empty[b]), lane);
           }
-          float2 th[8], tl[8];   // T_k of columns (cc + 2q, cc + 2q + 1): hi pair, lo pair
+          float2 th[4], tl[4];   // T_k of columns (cc + 2q, cc + 2q + 1): hi pair, lo pair
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 4; ++q) {
             const int j = 2 * q;
             float2 hi, lo;
             ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
@@ -277,31 +359,35 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
             tl[q] = mul2(lo, sc2);
           }
           if (direct) {
-            if (vi) {
+            // the product leaves through the write-out below: parked in the columns of y_1, free
+            // since the tile's sums were written out at its last weighted node
+            float h[8], l[8];
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                const int col = cc + 2 * q;
-                if (col < S.nfib) S.dout[(long long)col * S.n + i] = ff::to_f64(th[q].x, tl[q].x);
-                if (col + 1 < S.nfib) S.dout[(long long)(col + 1) * S.n + i] = ff::to_f64(th[q].y, tl[q].y);
-              }
+            for (int q = 0; q < 4; ++q) {
+              h[2 * q] = th[q].x;
+              h[2 * q + 1] = th[q].y;
+              l[2 * q] = tl[q].x;
+              l[2 * q + 1] = tl[q].y;
             }
+            tmem_st8(sums + (uint32_t)cc, h);
+            tmem_st8(sums + 32u + (uint32_t)cc, l);
             continue;
           }
 #pragma unroll
           for (int jj = 0; jj < P_; ++jj) {
-            const uint32_t sa = lane_base + FW_SUMS + 64u * jj + (uint32_t)cc;
-            float sh[16], sl[16];
+            const uint32_t sa = sums + 64u * jj + (uint32_t)cc;
+            float sh[8], sl[8];
             if (first) {
 #pragma unroll
-              for (int q = 0; q < 16; ++q) sh[q] = sl[q] = 0.0f;
+              for (int q = 0; q < 8; ++q) sh[q] = sl[q] = 0.0f;
             } else {
-              tmem_ld16(sa, sh);
-              tmem_ld16(sa + 32u, sl);
+              tmem_ld8(sa, sh);
+              tmem_ld8(sa + 32u, sl);
               tmem_wait_ld();
             }
             const float2 cj = S.c[jj];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 4; ++q) {
               float2 ah = make_float2(sh[2 * q], sh[2 * q + 1]), al = make_float2(sl[2 * q], sl[2 * q + 1]);
               ff::fma_ff2(ah, al, cj, th[q], tl[q]);
               sh[2 * q] = ah.x;
@@ -309,36 +395,22 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
               sl[2 * q] = al.x;
               sl[2 * q + 1] = al.y;
             }
-            if (!last) {
-              tmem_st16(sa, sh);
-              tmem_st16(sa + 32u, sl);
-            } else if (vi) {
-              const long long o = (long long)jj * J->stride + ybase;
-#pragma unroll
-              for (int q = 0; q < 16; ++q) {
-                const int col = cc + q;
-                if (col < S.nfib) {
-                  const long long e = o + (long long)col * S.n;
-                  if (y64) y64[e] = ff::to_f64(sh[q], sl[q]);
-                  else yff[e] = make_float2(sh[q], sl[q]);
-                  if (y2) y2[e] = ff::to_f64(sh[q], sl[q]);
-                  mx[jj] = max(mx[jj], __float_as_uint(sh[q]) & 0x7FFFFFFFu);
-                }
-              }
-            }
+            tmem_st8(sa, sh);
+            tmem_st8(sa + 32u, sl);
           }
         }
-        if (!direct && !last) tmem_wait_st();   // the sums are in TMEM before the next node reads them
-        if (last && J->out_exp) {
-#pragma unroll
-          for (int jj = 0; jj < P_; ++jj) {
-            uint32_t m = mx[jj];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-            // |y_j| < 2^{biased - 126}; a zero output keeps the slot's initial (very negative) value
-            const int emax = (int)(m >> 23);
-            if (lane == 0 && emax > 0) atomicMax(J->out_exp + jj, emax - 126);
-          }
+        tmem_wait_st();   // the sums (or the parked product) are in TMEM before they are read
+        if (direct) {
+          fw_write_out(sums, 1, ch, vi, i, lane, S.n, S.nfib, 0, nullptr, S.dout, nullptr, nullptr);
+        } else if (S.flags & FW_LAST) {
+          const FJob& J = P.jobs[S.job];
+          void* o = J.out_tab >= 0 ? (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out) : J.out;
+          void* o2 = J.out2_tab >= 0 ? (void*)((char*)P.ptrtab[J.out2_tab] + J.tab_off_out2) : J.out2;
+          const long long t0 = S.f0 * (long long)S.n;
+          float2* yff = J.out_f64 ? nullptr : reinterpret_cast<float2*>(o) + t0;
+          double* y64 = J.out_f64 ? reinterpret_cast<double*>(o) + t0 : nullptr;
+          double* y2 = o2 ? reinterpret_cast<double*>(o2) + t0 : nullptr;
+          fw_write_out(sums, P_, ch, vi, i, lane, S.n, S.nfib, J.stride, yff, y64, y2, J.out_exp);
         }
         ++sc;
         if (S.flags & FW_END) break;
@@ -355,7 +427,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
         while (true) {
           FwSlot S;
           const uint32_t b = sc & 1u, u = sc >> 1;
-          if (!fw_get(slots, slot_full, slot_empty, sc, S, wl)) ws_fail(abort_s, status);
+          if (!fw_get(slots, slot_full, slot_empty, sc, S, wl, -1)) ws_fail(abort_s, status);
           if (u >= 1 && !mbar_wait(smem_u32(&tmem_empty[b]), (u - 1) & 1u, wl)) ws_fail(abort_s, status);
           if (*abort_s) { stop = true; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
