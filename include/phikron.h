@@ -63,8 +63,14 @@ extern "C" {
                                          BF16 digit-slice products (Ozaki splitting, FP32
                                          accumulation in TMEM); state, node weights and the
                                          squaring recurrence in float-float (~48 bits);
-                                         1D exponentials in float64.  Needs every n[d] a
-                                         multiple of 16 in 16..4096, l_max <= 8, m <= 64.
+                                         1D exponentials in float64.  1 <= n[d] <= 4096,
+                                         l_max <= 20, m <= 64.  Sizes that are not a multiple
+                                         of 16 are zero-padded inside the plan to the next one
+                                         (the padded factor is diag(A^d, 0), whose exponentials
+                                         are diag(e^{cA^d}, I), so the pad stays zero): the
+                                         apply then scatters V into padded staging and gathers
+                                         the results (two extra elementwise passes); batched
+                                         applies need multiples of 16.
                                          The FP32 accumulation of a digit level is exact
                                          while its partial sums stay below 2^24 units; for
                                          long contractions (n[d] in the hundreds and more)

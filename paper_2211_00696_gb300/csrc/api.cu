@@ -231,6 +231,8 @@ int build_plan(Plan& P, int dims, const double* const* A, const int* n, double t
     P.N *= n[d];
   }
   for (int d = dims; d < PHIKRON_MAX_DIMS; ++d) P.n[d] = 1;
+  for (int d = 0; d < PHIKRON_MAX_DIMS; ++d) P.pn[d] = P.n[d];
+  P.PN = P.N;
 
   // alpha = tau * sum_d ||A^d||_inf  (Eq. (31))
   double alpha = 0.0;

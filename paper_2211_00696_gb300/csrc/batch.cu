@@ -82,6 +82,10 @@ int phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* 
       set_error("phikron_batch_create: every plan must use PHIKRON_PREC_OZAKI_BF16");
       return PHIKRON_ENOTSUP;
     }
+    if (P.PN != P.N) {
+      set_error("phikron_batch_create: batched plans need every n[d] a multiple of 16 (no padding)");
+      return PHIKRON_ENOTSUP;
+    }
     const int ks = mixed_slices(P);
     if (slices >= 0 && ks != slices) {
       set_error("phikron_batch_create: every plan must use the same digit-slice count");

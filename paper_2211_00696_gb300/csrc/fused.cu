@@ -80,23 +80,6 @@ struct FwSlot {
 };
 static_assert(sizeof(FwSlot) * FW_SLOTS <= FW_SLOT_BYTES, "slot ring");
 
-// all 256 epilogue threads (named barrier 1): true if any of them passes true
-__device__ __forceinline__ bool epi_vote_any256(bool pred) {
-  uint32_t r;
-  asm volatile(
-      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, 1, 256, q;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)pred)
-      : "memory");
-  return r != 0;
-}
-
-// one arrival of count 32 for the whole (converged) warp instead of 32 arrivals on one word
-__device__ __forceinline__ void mbar_arrive_warp(uint32_t mbar, int lane) {
-  __syncwarp();
-  if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], 32;" ::"r"(mbar) : "memory");
-}
-
 // reads slot sc once it is filled, then releases it: lane >= 0 for a whole warp (one arrival
 // of count 32), lane < 0 for a single thread
 __device__ __forceinline__ bool fw_get(const FwSlot* slots, uint64_t* slot_full, uint64_t* slot_empty, uint32_t sc,

@@ -258,6 +258,48 @@ __global__ void __launch_bounds__(EW_THREADS) g_expscan_kernel(const EJob* __res
   if (cur >= 0) block_exp_flush<1, 1022>(emax, jobs[cur].out_exp, red);
 }
 
+// sizes of a padded plan: n[d] of the caller's vectors, pn[d] of the padded ones (C-order)
+struct PadDims {
+  int dims;
+  int n[PHIKRON_MAX_DIMS];
+  int pn[PHIKRON_MAX_DIMS];
+};
+
+// Vp = V zero-padded: element q of the padded tensor takes V at the same multi-index when every
+// index is inside n, else 0
+__global__ void pad_scatter_kernel(const double* __restrict__ V, double* __restrict__ Vp, long long PN, PadDims D) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < PN; q += (long long)gridDim.x * blockDim.x) {
+    long long r = q, src = 0, mul = 1;
+    bool in = true;
+    for (int d = D.dims - 1; d >= 0; --d) {
+      const int id = (int)(r % D.pn[d]);
+      r /= D.pn[d];
+      in = in && id < D.n[d];
+      src += (long long)id * mul;
+      mul *= D.n[d];
+    }
+    Vp[q] = in ? V[src] : 0.0;
+  }
+}
+
+// Out[v][x] = Op[v][padded index of x] for the vectors v in mask (v < nvec <= 64)
+__global__ void pad_gather_kernel(const double* __restrict__ Op, double* __restrict__ Out, long long N, long long PN,
+                                  int nvec, unsigned long long mask, PadDims D) {
+  const long long total = (long long)nvec * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(t / N);
+    if (!((mask >> v) & 1ull)) continue;
+    long long r = t - (long long)v * N, dst = 0, mul = 1;
+    for (int d = D.dims - 1; d >= 0; --d) {
+      const int id = (int)(r % D.n[d]);
+      r /= D.n[d];
+      dst += (long long)id * mul;
+      mul *= D.pn[d];
+    }
+    Out[t] = Op[(long long)v * PN + dst];
+  }
+}
+
 // grid for a grid-stride elementwise kernel: every SM filled with resident blocks, no more
 // blocks than virtual blocks
 template <typename K>
@@ -388,6 +430,11 @@ struct MixedState {
   size_t mat_bytes[PHIKRON_MAX_DIMS] = {};
   int rexp_stride[PHIKRON_MAX_DIMS] = {};
   float2* dCoefFF = nullptr;
+  // padded plans (some n[d] not a multiple of 16): work buffers, input and output staging of the
+  // padded sizes; the apply scatters V into dVp and gathers the results from dOutp
+  bool padded = false;
+  double* dVp = nullptr;
+  double* dOutp = nullptr;
   Seq seq;                                         // launch sequence of a single-vector apply
 };
 
@@ -413,11 +460,18 @@ int precision_setup(Plan& P) {
     set_error("precision mode not supported");
     return PHIKRON_ENOTSUP;
   }
+  // the tensor-core mode products need every contracted size to be a multiple of 16: other
+  // sizes are padded (see Plan::pn)
+  bool pad = false;
+  P.PN = 1;
   for (int d = 0; d < P.dims; ++d) {
-    if (P.n[d] < 16 || P.n[d] > 4096 || P.n[d] % 16 != 0) {
-      set_error("mixed path: every n[d] must be a multiple of 16 in 16..4096");
+    P.pn[d] = std::max(16, (P.n[d] + 15) / 16 * 16);
+    if (P.pn[d] > 4096) {
+      set_error("mixed path: every n[d] must be at most 4096");
       return PHIKRON_ENOTSUP;
     }
+    pad = pad || P.pn[d] != P.n[d];
+    P.PN *= P.pn[d];
   }
   if (P.p > MAXP || P.m > MAXM) {
     set_error("mixed path: needs l_max <= 20 and at most 64 quadrature nodes");
@@ -445,16 +499,26 @@ int precision_setup(Plan& P) {
 
   // slice every 1D exponential (plan time, host)
   for (int u = 0; u < P.nuniq; ++u) {
-    const int nd = P.n[P.uniq_rep[u]];
-    const size_t nn = (size_t)nd * nd;
+    const int nd = P.n[P.uniq_rep[u]], pd = P.pn[P.uniq_rep[u]];
+    const size_t nn = (size_t)nd * nd, pp = (size_t)pd * pd;
     std::vector<double> h(nn * P.nexp);
     PK_TRY_CUDA(cudaMemcpy(h.data(), P.dExp[u], sizeof(double) * nn * P.nexp, cudaMemcpyDeviceToHost));
-    const size_t mb = sliced_bytes(nd, slices);
-    const int rs = 128 * ((nd + 127) / 128);
+    const size_t mb = sliced_bytes(pd, slices);
+    const int rs = 128 * ((pd + 127) / 128);
     std::vector<uint8_t> sl(mb * P.nexp);
     std::vector<int> rx((size_t)rs * P.nexp);
-    for (int e = 0; e < P.nexp; ++e)
-      slice_matrix_host(h.data() + nn * e, nd, slices, sl.data() + mb * e, rx.data() + (size_t)rs * e);
+    std::vector<double> hp(pp);
+    for (int e = 0; e < P.nexp; ++e) {
+      const double* src = h.data() + nn * e;
+      if (pd != nd) {   // exp of diag(c A^d, 0): the exponential on the leading block, I on the pad
+        std::fill(hp.begin(), hp.end(), 0.0);
+        for (int r = 0; r < nd; ++r)
+          std::copy(src + (size_t)r * nd, src + (size_t)(r + 1) * nd, hp.data() + (size_t)r * pd);
+        for (int r = nd; r < pd; ++r) hp[(size_t)r * pd + r] = 1.0;
+        src = hp.data();
+      }
+      slice_matrix_host(src, pd, slices, sl.data() + mb * e, rx.data() + (size_t)rs * e);
+    }
     PK_RET(P.alloc((void**)&M->dSl[u], sl.size()));
     PK_RET(P.alloc((void**)&M->dRexp[u], sizeof(int) * rx.size()));
     PK_TRY_CUDA(cudaMemcpy(M->dSl[u], sl.data(), sl.size(), cudaMemcpyHostToDevice));
@@ -472,7 +536,8 @@ int precision_setup(Plan& P) {
   if (!cf.empty())
     PK_TRY_CUDA(cudaMemcpy(M->dCoefFF, cf.data(), sizeof(float2) * cf.size(), cudaMemcpyHostToDevice));
 
-  // the single-vector apply as a launch sequence over the plan's own work buffers
+  // the single-vector apply as a launch sequence over the plan's own work buffers (of the
+  // padded sizes, with input and output staging, when some n[d] is padded)
   std::vector<SeqUnit> units(1);
   units[0].plan = &P;
   units[0].inst = 0;
@@ -481,6 +546,19 @@ int precision_setup(Plan& P) {
   units[0].W2 = reinterpret_cast<float2*>(P.dW2);
   units[0].Y = reinterpret_cast<float2*>(P.dY);
   units[0].Yn = reinterpret_cast<float2*>(P.dYn);
+  M->padded = pad;
+  if (pad) {
+    const size_t nv = (size_t)std::max(P.m + 2, std::max(P.p, 1));
+    const size_t ny = (size_t)std::max(P.p, 1);
+    const size_t nout = (size_t)(P.p + 1) * (P.opts.half_step ? 2 : 1);
+    PK_RET(P.alloc((void**)&units[0].W1, sizeof(float2) * nv * P.PN));
+    PK_RET(P.alloc((void**)&units[0].W2, sizeof(float2) * nv * P.PN));
+    PK_RET(P.alloc((void**)&units[0].Y, sizeof(float2) * ny * P.PN));
+    PK_RET(P.alloc((void**)&units[0].Yn, sizeof(float2) * ny * P.PN));
+    PK_RET(P.alloc((void**)&M->dVp, sizeof(double) * P.PN));
+    PK_RET(P.alloc((void**)&M->dOutp, sizeof(double) * nout * P.PN));
+    PK_TRY_CUDA(cudaMemset(M->dOutp, 0, sizeof(double) * nout * P.PN));
+  }
   SeqConfig cfg;
   cfg.half = P.opts.half_step != 0;
   cfg.slices = slices;
@@ -499,9 +577,35 @@ int apply_mixed(Plan& P, const double* V, double* Out, cudaStream_t st) {
   MixedState& M = *static_cast<MixedState*>(P.mixed);
   PtrArgs args{};
   args.n = 2;
-  args.p[0] = const_cast<double*>(V);
-  args.p[1] = Out;
-  return seq_run(M.seq, args, st);
+  if (!M.padded) {
+    args.p[0] = const_cast<double*>(V);
+    args.p[1] = Out;
+    return seq_run(M.seq, args, st);
+  }
+  PadDims D{};
+  D.dims = P.dims;
+  for (int d = 0; d < P.dims; ++d) {
+    D.n[d] = P.n[d];
+    D.pn[d] = P.pn[d];
+  }
+  launch_begin(KC_CONVERT, st);
+  pad_scatter_kernel<<<ew_grid(pad_scatter_kernel, (P.PN + 255) / 256), 256, 0, st>>>(V, M.dVp, P.PN, D);
+  launch_end(st);
+  PK_CHECK_LAUNCH();
+  args.p[0] = M.dVp;
+  args.p[1] = M.dOutp;
+  PK_RET(seq_run(M.seq, args, st));
+  // every output vector except the phi_0 slots a skip_phi0 plan leaves untouched
+  const int nout = (P.p + 1) * (P.opts.half_step ? 2 : 1);
+  unsigned long long mask = 0;
+  for (int v = 0; v < nout; ++v)
+    if (!(P.opts.skip_phi0 && (v % (P.p + 1)) == 0)) mask |= 1ull << v;
+  launch_begin(KC_CONVERT, st);
+  pad_gather_kernel<<<ew_grid(pad_gather_kernel, (nout * P.N + 255) / 256), 256, 0, st>>>(M.dOutp, Out, P.N, P.PN,
+                                                                                        nout, mask, D);
+  launch_end(st);
+  PK_CHECK_LAUNCH();
+  return PHIKRON_OK;
 }
 
 int mixed_slices(const Plan& P) { return static_cast<const MixedState*>(P.mixed)->slices; }
@@ -695,9 +799,9 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
     for (int u = 0; u < nu; ++u) {
       const Plan& P = *units[u].plan;
       EJob j{};
-      j.N = P.N;
+      j.N = P.PN;
       j.v_tab = 2 * units[u].inst;
-      j.tab_off_v = (long long)units[u].rhs * P.N * 8;
+      j.tab_off_v = (long long)units[u].rhs * P.PN * 8;
       j.out_tab = j.out2_tab = -1;
       j.out_exp = slots + us[u].vslot;
       ej.push_back(j);
@@ -732,15 +836,15 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
         const CV& c = vs[q];
         const Plan& P = *units[c.u].plan;
         long long B0 = 1, R = 1;
-        for (int e = 0; e < d; ++e) B0 *= P.n[e];
-        for (int e = d + 1; e < dims; ++e) R *= P.n[e];
+        for (int e = 0; e < d; ++e) B0 *= P.pn[e];
+        for (int e = d + 1; e < dims; ++e) R *= P.pn[e];
         trans = R > 1;
         const MixedView mv = mixed_view(P, d);
-        const long long N = P.N;
+        const long long N = P.PN;
         float2* dst = (d % 2 == 0) ? units[c.u].W1 : units[c.u].W2;
         const float2* src = (d % 2 == 0) ? units[c.u].W2 : units[c.u].W1;
         GJob j{};
-        j.n = P.n[d];
+        j.n = P.pn[d];
         j.R = R;
         j.B0 = B0;
         j.eslices = mv.sl + mv.mat_bytes * (size_t)c.mat;
@@ -803,7 +907,7 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
   // >= 2) over a factor of at most FW_MAXN rows and 1 <= p <= FW_MAXP.
   bool fuse = cfg.fuse && p >= 1 && p <= FW_MAXP && dims >= 2;
   for (int u = 0; u < nu && fuse; ++u)
-    if (units[u].plan->n[dims - 1] > FW_MAXN) fuse = false;
+    if (units[u].plan->pn[dims - 1] > FW_MAXN) fuse = false;
   S.fused = fuse;
   std::vector<float2*> T(nu);
   std::vector<int> tslot(nu);
@@ -815,12 +919,12 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       tslot[u] = us[u].next;
       us[u].next += P.m;
       for (int k = 0; k < P.m; ++k)
-        vs.push_back(CV{u, k, nullptr, us[u].vslot, true, k, T[u] + (size_t)k * P.N, false, 0, false, tslot[u] + k});
+        vs.push_back(CV{u, k, nullptr, us[u].vslot, true, k, T[u] + (size_t)k * P.PN, false, 0, false, tslot[u] + k});
       if (!P.opts.skip_phi0)
         vs.push_back(CV{u, P.m, nullptr, us[u].vslot, true, P.m, nullptr, true, 0, true, -1});
       if (cfg.half && !P.opts.skip_phi0)
         vs.push_back(CV{u, P.m + P.s, nullptr, us[u].vslot, true, P.m + 1, nullptr, true,
-                        (long long)(p + 1) * P.N * 8, true, -1});
+                        (long long)(p + 1) * P.PN * 8, true, -1});
     }
     if (!fuse) {
       PK_RET(chain(vs, true, dims, nullptr));
@@ -837,16 +941,16 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
         const MixedView mv = mixed_view(P, dl);
         const float2* src = (dl % 2 == 1) ? units[u].W1 : units[u].W2;   // written by pass dl - 1
         FJob j{};
-        j.n = P.n[dl];
-        j.B0 = P.N / P.n[dl];
+        j.n = P.pn[dl];
+        j.B0 = P.PN / P.pn[dl];
         j.node0 = (int)fn.size();
         j.m = P.m;
         j.coef = mv.coef;
-        j.stride = P.N;
+        j.stride = P.PN;
         j.out_tab = j.out2_tab = -1;
         if (P.s == 0) {
           j.out_tab = 2 * units[u].inst + 1;
-          j.tab_off_out = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)P.N * 8;
+          j.tab_off_out = (long long)units[u].rhs * out_mult * P.PN * 8 + (long long)P.PN * 8;
           j.out_f64 = 1;
         } else {
           j.out = us[u].Y;
@@ -856,13 +960,13 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
         }
         if (cfg.half && P.s == 1) {
           j.out2_tab = 2 * units[u].inst + 1;
-          j.tab_off_out2 = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)(p + 2) * P.N * 8;
+          j.tab_off_out2 = (long long)units[u].rhs * out_mult * P.PN * 8 + (long long)(p + 2) * P.PN * 8;
         }
         // the vectors of this unit in vs are contiguous, in the order pushed above
         for (; q < vs.size() && vs[q].u == u; ++q) {
           const CV& c = vs[q];
           FNode nd{};
-          nd.in = src + (size_t)c.vec * P.N;
+          nd.in = src + (size_t)c.vec * P.PN;
           nd.in_exp = slots + cur[q];
           nd.eslices = mv.sl + mv.mat_bytes * (size_t)c.mat;
           nd.rexp = mv.rexp + (size_t)mv.rexp_stride * c.mat;
@@ -870,7 +974,7 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
           if (c.out_tab) {   // phi_0 (or phi_0 at tau/2): stored as it is, float64
             nd.direct = 1;
             nd.out_tab = 2 * units[u].inst + 1;
-            nd.tab_off_out = (long long)units[u].rhs * out_mult * P.N * 8 + c.out_off;
+            nd.tab_off_out = (long long)units[u].rhs * out_mult * P.PN * 8 + c.out_off;
           } else {
             nd.direct = 0;
             nd.k = c.mat;
@@ -896,12 +1000,12 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       j.a = T[u];
       j.coef = mv.coef;
       j.m = P.m;
-      j.N = P.N;
-      j.stride = P.N;
+      j.N = P.PN;
+      j.stride = P.PN;
       j.out_tab = j.out2_tab = -1;
       if (P.s == 0) {
         j.out_tab = 2 * units[u].inst + 1;
-        j.tab_off_out = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)P.N * 8;
+        j.tab_off_out = (long long)units[u].rhs * out_mult * P.PN * 8 + (long long)P.PN * 8;
         j.out_f64 = 1;
       } else {
         j.out = us[u].Y;
@@ -911,7 +1015,7 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       }
       if (cfg.half && P.s == 1) {
         j.out2_tab = 2 * units[u].inst + 1;
-        j.tab_off_out2 = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)(p + 2) * P.N * 8;
+        j.tab_off_out2 = (long long)units[u].rhs * out_mult * P.PN * 8 + (long long)(p + 2) * P.PN * 8;
       }
       ej.push_back(j);
     }
@@ -928,8 +1032,8 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
         part.push_back(u);
         float2* Z = (dims % 2 == 1) ? units[u].W1 : units[u].W2;
         for (int i = 0; i < p; ++i)
-          vs.push_back(CV{u, P.m + 1 + t, us[u].Y + (size_t)i * P.N, us[u].yslot + i, false, i,
-                          Z + (size_t)i * P.N, false, 0, false, -1});
+          vs.push_back(CV{u, P.m + 1 + t, us[u].Y + (size_t)i * P.PN, us[u].yslot + i, false, i,
+                          Z + (size_t)i * P.PN, false, 0, false, -1});
       }
       PK_RET(chain(vs, false, dims, nullptr));
       std::vector<EJob> sj;
@@ -938,13 +1042,13 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
         EJob j{};
         j.a = (dims % 2 == 1) ? units[u].W1 : units[u].W2;
         j.b = us[u].Y;
-        j.N = P.N;
-        j.stride = P.N;
+        j.N = P.PN;
+        j.stride = P.PN;
         j.out_tab = j.out2_tab = -1;
         const bool lastt = (t == P.s - 1);
         if (lastt) {
           j.out_tab = 2 * units[u].inst + 1;
-          j.tab_off_out = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)P.N * 8;
+          j.tab_off_out = (long long)units[u].rhs * out_mult * P.PN * 8 + (long long)P.PN * 8;
           j.out_f64 = 1;
         } else {
           j.out = us[u].Yn;
@@ -955,7 +1059,7 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
         }
         if (cfg.half && t == P.s - 2) {
           j.out2_tab = 2 * units[u].inst + 1;
-          j.tab_off_out2 = (long long)units[u].rhs * out_mult * P.N * 8 + (long long)(p + 2) * P.N * 8;
+          j.tab_off_out2 = (long long)units[u].rhs * out_mult * P.PN * 8 + (long long)(p + 2) * P.PN * 8;
         }
         sj.push_back(j);
         if (!lastt) std::swap(us[u].Y, us[u].Yn);

@@ -12,6 +12,11 @@ struct Plan {
   int dims = 0;
   int n[PHIKRON_MAX_DIMS] = {1, 1, 1, 1, 1, 1};
   long long N = 0;
+  // sizes the mixed path computes with: n[d] rounded up to a multiple of 16 (the padded factor
+  // is diag(A^d, 0), so its exponentials are diag(e^{c A^d}, I) and a zero-padded vector stays
+  // zero on the pad); equal to n, N otherwise
+  int pn[PHIKRON_MAX_DIMS] = {1, 1, 1, 1, 1, 1};
+  long long PN = 0;
   double tau = 0.0;
   int p = 0;            // l_max: orders 0..p are returned
   double tol = 0.0;

@@ -136,8 +136,12 @@ def test_mixed_edge_cases():
 
 def test_mixed_rejects_unsupported_sizes():
     pk = _pk()
-    with pytest.raises(pk.PhikronError):
-        pk.Plan([W.laplacian_factor(20), W.laplacian_factor(32)], 1e-3, 2, 1e-8, precision=pk.PREC_OZAKI_BF16)
+    # padded plans (a size not a multiple of 16) are not batched
+    padded = pk.Plan([W.laplacian_factor(20), W.laplacian_factor(32)], 1e-3, 2, 1e-8, precision=pk.PREC_OZAKI_BF16)
+    with pytest.raises(pk.PhikronError) as e:
+        pk.Batch([padded], nrhs=1)
+    assert e.value.code == pk.phikron.ENOTSUP
+    padded.close()
     with pytest.raises(pk.PhikronError):     # above the 4096 limit of the mixed path
         pk.Plan([W.laplacian_factor(4112), W.laplacian_factor(16)], 1e-6, 1, 1e-8, precision=pk.PREC_OZAKI_BF16)
 
