@@ -149,7 +149,7 @@ def peaks():
 # profiles/mode_kernel_ws_convdiff3d_n128_ncu_full.md (one launch of the z-mode node pass:
 # 11 vectors x N unknowns); valid only while the kernel code is the one captured (hash of
 # tc_mode.cu without comments and blank lines, see code_hash).
-PROFILED_MODE_TRAFFIC = {"source_sha256_16": "a109ed270605a2db", "bytes": 186.070784e6 + 128.555008e6,
+PROFILED_MODE_TRAFFIC = {"source_sha256_16": "594c79b1a171748d", "bytes": 186.084608e6 + 128.727808e6,
                          "vector_passes": 11, "N": 2097152}
 
 
@@ -356,9 +356,33 @@ def run_batched(args):
     ms = e0.elapsed_time(e1) / args.steps
     unknowns = 4 * sum(int(np.prod(d["shape"])) for d in insts)
     info = batch.info()
+    # per-kernel CUDA-event times of further applies (separate pass, same stream, no graph)
+    batch.profile_begin(8192)
+    for _ in range(2):
+        batch.apply(V, out)
+    torch.cuda.synchronize()
+    prof = batch.profile_end()
+    # algorithmic work of the tensor-core mode passes: every (vector, mode) product reads and
+    # writes one 8-byte state per unknown and does slices (slices + 1) / 2 BF16 slice products
+    # of 2 N n_d flops; per unit, m + s p + 1 actions plus phi_0 at tau/2
+    hbm, fl = 0.0, 0.0
+    for d, p_ in zip(insts, plans):
+        pi = p_.info()
+        Ni = int(np.prod(d["shape"]))
+        acts = pi["actions"] + 1
+        hbm += 4 * acts * 3 * 16.0 * Ni
+        fl += 4 * acts * 2.0 * Ni * sum(d["shape"]) * (3 * 4 // 2)
+    pk_, src = peaks()
+    t = prof["ms"]["tc_mode"] / 2 * 1e-3
+    gbs, tfl = hbm / t / 1e9, fl / t / 1e12
+    roof = {"bound": "hbm", "kernel": "tc mode-product kernels (tcgen05 BF16 digit slices)", "achieved": gbs,
+            "peak": pk_.get("hbm_gbs", 6800.0), "unit": "GB/s", "frac": gbs / pk_.get("hbm_gbs", 6800.0),
+            "peak_source": f"{src} hbm_gbs", "tensor_frac": tfl / pk_.get("bf16_tflops", 1900.0),
+            "mode_ms_per_step": t * 1e3, "kernel_ms_per_step": {k: v_ / 2 for k, v_ in prof["ms"].items() if v_ > 0},
+            "traffic": None}
     print(json.dumps({"metric": "batched phi_0..3 at tau and tau/2, unknowns/s", "value": unknowns / (ms * 1e-3),
                       "unit": UNIT, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
-                      "unknowns_per_step": unknowns, "plan_and_batch_ms": plan_ms,
+                      "unknowns_per_step": unknowns, "plan_and_batch_ms": plan_ms, "roofline": roof,
                       "config": {"workload": "batched_uneven3d_32x4rhs", "slices": 3,
                                  "s": [p.info()["s"] for p in plans], "m": [p.info()["m"] for p in plans]},
                       "batch": info}), flush=True)
@@ -395,21 +419,74 @@ def run_allen_cahn(args):
             it.check_status()
             ms = e0.elapsed_time(e1)
             info = it.info()
-            it.close()
             finals[prec] = U.cpu().numpy()
+            # per-kernel CUDA-event times of a few more steps (separate pass, same stream)
+            prof_steps = 5
+            it.profile_begin(4096)
+            it.step(U, prof_steps)
+            torch.cuda.synchronize()
+            prof = it.profile_end()
+            slices = 0 if prec == "fp64" else it_slices(fac, pid, tol)
+            it.close()
             res[f"{method}_{prec}"] = {"ms_total": ms, "ms_per_step": ms / nsteps,
                                        "unknown_steps_per_s": N * nsteps / (ms * 1e-3),
                                        "plans": {"c": info["c"][:info["nplans"]], "s": info["s"][:info["nplans"]],
-                                                 "m": info["m"][:info["nplans"]]}}
+                                                 "m": info["m"][:info["nplans"]],
+                                                 "actions": info["actions"][:info["nplans"]]},
+                                       "kernel_ms_per_step": {k: v_ / prof_steps for k, v_ in prof["ms"].items() if v_ > 0},
+                                       "roofline": integrator_roofline(info, prof, prof_steps, N, fac[0].shape[0],
+                                                                       len(fac), slices)}
         d = np.linalg.norm(finals["mixed"] - finals["fp64"]) / np.linalg.norm(finals["fp64"])
         res[f"{method}_final_rel_diff_mixed_vs_fp64"] = float(d)
     line = {"metric": "Allen-Cahn 2048^2 exponential integrators, unknowns x steps / s (mixed)",
             "value": res["euler_mixed"]["unknown_steps_per_s"], "unit": "unknown-steps/s", "steps": nsteps,
+            "roofline": res["euler_mixed"]["roofline"],
             "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "allen_cahn2d_2048_periodic_eps0.01_tau1e-2", "N": N, "time_steps": nsteps},
             "results": res,
             "gate_final_rel_diff_le_1e-6": all(res[f"{m}_final_rel_diff_mixed_vs_fp64"] <= 1e-6 for m in ("euler", "rk2"))}
     print(json.dumps(line), flush=True)
+
+
+def it_slices(fac, pid, tol):
+    """Digit slices of the integrator's mixed plans (same rule as phikron_plan's default)."""
+    import paper_2211_00696_gb300 as pk
+    plan = pk.Plan(fac, 1e-2, 1, tol, precision=pid)
+    k = plan.info()["slices"]
+    plan.close()
+    return k
+
+
+def integrator_roofline(info, prof, steps, N, n, dims, slices):
+    """Roofline of the mode-product kernels of an integrator run.  Every plan is applied once per
+    step (exponential Euler: one plan; the two-stage method: c2 and 1); a plan's apply runs
+    `actions` Kronecker actions of dims mode products of 2 N n flops each.  Mixed path: BF16
+    tensor work = slices (slices + 1) / 2 slice-pair products per mode product, against the
+    sustained BF16 peak (the kernels run inside a long step); float64 path: DFMA work against the
+    nominal FP64 rate."""
+    pk_, src = peaks()
+    actions = sum(info["actions"][:info["nplans"]])
+    flops = actions * dims * 2.0 * N * n          # per step, the method's own flops
+    hbm_bytes = actions * dims * 16.0 * N         # one 8-byte state read and written per mode product
+    if slices:
+        t = prof["ms"]["tc_mode"] / steps * 1e-3
+        if t <= 0:
+            return None
+        tfl = flops * (slices * (slices + 1) // 2) / t / 1e12
+        peak = pk_.get("bf16_tflops_sustained", 1700.0)
+        return {"bound": "tensor", "kernel": "tc mode-product kernels (tcgen05 BF16 digit slices)",
+                "achieved": tfl, "peak": peak, "unit": "TFLOP/s", "frac": tfl / peak,
+                "peak_source": f"{src} bf16_tflops_sustained", "hbm_frac": hbm_bytes / t / 1e9 / pk_.get("hbm_gbs", 6800.0),
+                "slice_pair_flops_per_step": flops * (slices * (slices + 1) // 2),
+                "mode_ms_per_step": t * 1e3, "traffic": None}
+    t = prof["ms"]["gemm_f64"] / steps * 1e-3
+    if t <= 0:
+        return None
+    peak = 152 * 4 * 2.070e9 / 1e12
+    ach = flops / t / 1e12
+    return {"bound": "alu", "kernel": "gemm_f64_kernel (DFMA mode products)", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "peak_source": "nominal FP64 rate (152 SMs x 4 flop/clk x 2070 MHz)",
+            "mode_ms_per_step": t * 1e3, "traffic": None}
 
 
 def fp64_gpu_compare(prob, V, out_shape, flush, golden, dev, local, tol, steps=3):

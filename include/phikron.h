@@ -283,6 +283,10 @@ int  phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t*
 int  phikron_batch_apply(phikron_batch_t batch, const double* const* V, double* const* Out, void* stream);
 int  phikron_batch_get_info(phikron_batch_t batch, phikron_batch_info* info);
 int  phikron_batch_check_status(phikron_batch_t batch);
+/* Per-kernel timing of batched applies, as phikron_profile_begin/end (timed applies run the
+ * launch sequence without its CUDA graph, one event pair per kernel). */
+int  phikron_batch_profile_begin(phikron_batch_t batch, int max_timed);
+int  phikron_batch_profile_end(phikron_batch_t batch, struct phikron_profile* out);
 void phikron_batch_destroy(phikron_batch_t batch);
 
 /* ------------------------------------------------------------------ learned (s, m) selector
@@ -447,6 +451,11 @@ int  phikron_erk_create(phikron_erk_t* out, int method, int dims, const double* 
 int  phikron_erk_step(phikron_erk_t erk, double* U, int nsteps, void* stream);
 int  phikron_erk_get_info(phikron_erk_t erk, phikron_erk_info* info);
 int  phikron_erk_check_status(phikron_erk_t erk);
+/* Per-kernel timing of an integrator: as phikron_profile_begin/end, over the launches of its
+ * plans' applies and of its own kernels (stencil A u, residuals, stage combinations: class 5),
+ * summed per class. */
+int  phikron_erk_profile_begin(phikron_erk_t erk, int max_timed);
+int  phikron_erk_profile_end(phikron_erk_t erk, phikron_profile* out);
 void phikron_erk_destroy(phikron_erk_t erk);
 
 #ifdef __cplusplus

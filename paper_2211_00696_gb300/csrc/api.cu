@@ -135,6 +135,36 @@ int Plan::alloc(void** p, size_t bytes) {
   return PHIKRON_OK;
 }
 
+int profiler_begin(Profiler& pr, int max_timed) {
+  pr.launches = 0;
+  for (int c = 0; c < KC_COUNT; ++c) pr.launches_by_class[c] = 0;
+  pr.used = 0;
+  while ((int)pr.cls.size() < max_timed) {
+    cudaEvent_t a, b;
+    PK_TRY_CUDA(cudaEventCreate(&a));
+    PK_TRY_CUDA(cudaEventCreate(&b));
+    pr.ev.push_back(a);
+    pr.ev.push_back(b);
+    pr.cls.push_back(0);
+  }
+  pr.timing = max_timed > 0;
+  return PHIKRON_OK;
+}
+
+int profiler_end(Profiler& pr, phikron_profile* out) {
+  for (int c = 0; c < KC_COUNT; ++c) out->launches[c] += pr.launches_by_class[c];
+  for (size_t i = 0; i < pr.used; ++i) {
+    PK_TRY_CUDA(cudaEventSynchronize(pr.ev[2 * i + 1]));
+    float ms = 0.f;
+    PK_TRY_CUDA(cudaEventElapsedTime(&ms, pr.ev[2 * i], pr.ev[2 * i + 1]));
+    out->ms[pr.cls[i]] += ms;
+  }
+  out->timed_launches += (long long)pr.used;
+  pr.timing = false;
+  pr.used = 0;
+  return PHIKRON_OK;
+}
+
 void selector_features(int dims, const int* n, const double* tau_norm_inf, int p, double tol, float* out) {
   for (int d = 0; d < 3; ++d) {
     if (d < dims) {
@@ -910,42 +940,18 @@ int phikron_check_status(phikron_plan_t plan) {
 int phikron_profile_begin(phikron_plan_t plan, int max_timed) {
   clear_error();
   if (!plan || max_timed < 0) { set_error("phikron_profile_begin: bad arguments"); return PHIKRON_EINVAL; }
-  Profiler& pr = plan->impl.prof;
   DeviceGuard dg(plan->impl.opts.device);
   if (dg.rc != PHIKRON_OK) return dg.rc;
-  pr.launches = 0;
-  for (int c = 0; c < KC_COUNT; ++c) pr.launches_by_class[c] = 0;
-  pr.used = 0;
-  while ((int)pr.cls.size() < max_timed) {
-    cudaEvent_t a, b;
-    PK_TRY_CUDA(cudaEventCreate(&a));
-    PK_TRY_CUDA(cudaEventCreate(&b));
-    pr.ev.push_back(a);
-    pr.ev.push_back(b);
-    pr.cls.push_back(0);
-  }
-  pr.timing = max_timed > 0;
-  return PHIKRON_OK;
+  return profiler_begin(plan->impl.prof, max_timed);
 }
 
 int phikron_profile_end(phikron_plan_t plan, phikron_profile* out) {
   clear_error();
   if (!plan || !out) { set_error("phikron_profile_end: NULL argument"); return PHIKRON_EINVAL; }
-  Profiler& pr = plan->impl.prof;
   DeviceGuard dg(plan->impl.opts.device);
   if (dg.rc != PHIKRON_OK) return dg.rc;
   std::memset(out, 0, sizeof(*out));
-  for (int c = 0; c < KC_COUNT; ++c) out->launches[c] = pr.launches_by_class[c];
-  for (size_t i = 0; i < pr.used; ++i) {
-    PK_TRY_CUDA(cudaEventSynchronize(pr.ev[2 * i + 1]));
-    float ms = 0.f;
-    PK_TRY_CUDA(cudaEventElapsedTime(&ms, pr.ev[2 * i], pr.ev[2 * i + 1]));
-    out->ms[pr.cls[i]] += ms;
-  }
-  out->timed_launches = (long long)pr.used;
-  pr.timing = false;
-  pr.used = 0;
-  return PHIKRON_OK;
+  return profiler_end(plan->impl.prof, out);
 }
 
 int phikron_log_quaderr(double n, int p, double alpha, double beta, int rule, double* log_err) {

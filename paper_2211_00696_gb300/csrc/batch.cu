@@ -16,6 +16,7 @@ using namespace phikron;
 
 
 struct phikron_batch_s {
+  Profiler prof;   // launches of the applies (timing: phikron_batch_profile_begin/end)
   std::vector<const Plan*> plans;
   int nrhs = 1;
   bool half = false;
@@ -238,9 +239,31 @@ int phikron_batch_apply(phikron_batch_t b, const double* const* V, double* const
     cudaEventDestroy(e1);
     b->tuned = true;
   }
-  if (rc == PHIKRON_OK) rc = seq_run(*b->cand[b->chosen], args, st);
+  if (rc == PHIKRON_OK) {
+    ProfScope ps(&b->prof);
+    rc = seq_run(*b->cand[b->chosen], args, st);
+  }
   if (b->device >= 0 && b->device != prev) cudaSetDevice(prev);
   return rc;
+}
+
+int phikron_batch_profile_begin(phikron_batch_t b, int max_timed) {
+  clear_error();
+  if (!b || max_timed < 0) {
+    set_error("phikron_batch_profile_begin: bad arguments");
+    return PHIKRON_EINVAL;
+  }
+  return profiler_begin(b->prof, max_timed);
+}
+
+int phikron_batch_profile_end(phikron_batch_t b, phikron_profile* out) {
+  clear_error();
+  if (!b || !out) {
+    set_error("phikron_batch_profile_end: NULL argument");
+    return PHIKRON_EINVAL;
+  }
+  *out = phikron_profile{};
+  return profiler_end(b->prof, out);
 }
 
 int phikron_batch_get_info(phikron_batch_t b, phikron_batch_info* info) {

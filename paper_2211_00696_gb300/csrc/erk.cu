@@ -97,6 +97,7 @@ int ew_blocks(long long N) { return (int)std::max(1LL, std::min((N + EW - 1) / E
 using namespace phikron;
 
 struct phikron_erk_s {
+  phikron::Profiler prof;   // the integrator's own kernels (stencil, residual, stage combinations)
   int method = 0, dims = 0, nonlin = 0;
   int n[PHIKRON_MAX_DIMS] = {1, 1, 1, 1, 1, 1};
   long long N = 0;
@@ -302,6 +303,7 @@ int phikron_erk_step(phikron_erk_t erk, double* U, int nsteps, void* stream) {
   if (erk->device >= 0 && erk->device != prev) cudaSetDevice(erk->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = PHIKRON_OK;
+  ProfScope ps(&erk->prof);
   for (int k = 0; k < nsteps && rc == PHIKRON_OK; ++k) rc = erk_step(*erk, U, st);
   if (erk->device >= 0 && erk->device != prev) cudaSetDevice(prev);
   return rc;
@@ -333,6 +335,31 @@ int phikron_erk_check_status(phikron_erk_t erk) {
     const int rc = phikron_check_status(p);
     if (rc != PHIKRON_OK) return rc;
   }
+  return PHIKRON_OK;
+}
+
+int phikron_erk_profile_begin(phikron_erk_t erk, int max_timed) {
+  clear_error();
+  if (!erk || max_timed < 0) { set_error("phikron_erk_profile_begin: bad arguments"); return PHIKRON_EINVAL; }
+  for (phikron_plan_t p : erk->plans) PK_RET(phikron_profile_begin(p, max_timed));
+  return profiler_begin(erk->prof, max_timed);
+}
+
+int phikron_erk_profile_end(phikron_erk_t erk, phikron_profile* out) {
+  clear_error();
+  if (!erk || !out) { set_error("phikron_erk_profile_end: NULL argument"); return PHIKRON_EINVAL; }
+  phikron_profile sum{};
+  for (phikron_plan_t p : erk->plans) {
+    phikron_profile one{};
+    PK_RET(phikron_profile_end(p, &one));
+    for (int c = 0; c < PHIKRON_KERNEL_CLASSES; ++c) {
+      sum.ms[c] += one.ms[c];
+      sum.launches[c] += one.launches[c];
+    }
+    sum.timed_launches += one.timed_launches;
+  }
+  PK_RET(profiler_end(erk->prof, &sum));
+  *out = sum;
   return PHIKRON_OK;
 }
 

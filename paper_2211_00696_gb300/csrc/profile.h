@@ -10,6 +10,8 @@
 
 #include <vector>
 
+#include "../../include/phikron.h"
+
 namespace phikron {
 
 enum KernelClass {
@@ -35,6 +37,11 @@ struct Profiler {
 };
 
 extern thread_local Profiler* tl_prof;
+
+// Starts counting (and, for max_timed > 0, timing the first max_timed) launches; profiler_end
+// adds the counts and the summed event times per class to *out and stops timing.
+int profiler_begin(Profiler& pr, int max_timed);
+int profiler_end(Profiler& pr, struct ::phikron_profile* out);
 
 inline void launch_begin(int c, cudaStream_t st) {
   Profiler* p = tl_prof;

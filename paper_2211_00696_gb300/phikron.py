@@ -95,6 +95,10 @@ SIGNATURES = {
     "phikron_erk_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "phikron_erk_get_info": (C.c_int, [C.c_void_p, C.POINTER(ErkInfo)]),
     "phikron_erk_check_status": (C.c_int, [C.c_void_p]),
+    "phikron_erk_profile_begin": (C.c_int, [C.c_void_p, C.c_int]),
+    "phikron_batch_profile_begin": (C.c_int, [C.c_void_p, C.c_int]),
+    "phikron_batch_profile_end": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
+    "phikron_erk_profile_end": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "phikron_erk_destroy": (None, [C.c_void_p]),
     "phikron_selector_features": (C.c_int, [C.c_int, _IP, _DP, C.c_int, C.c_double, C.POINTER(C.c_float)]),
     "phikron_selector_criterion": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _DP]),
@@ -353,6 +357,17 @@ class Batch:
         _check(lib().phikron_batch_get_info(self._h, C.byref(inf)))
         return {k: getattr(inf, k) for k, _ in BatchInfo._fields_}
 
+    def profile_begin(self, max_timed: int = 0):
+        """Count (and, if max_timed > 0, event-time) the kernels of the following applies."""
+        _check(lib().phikron_batch_profile_begin(self._h, max_timed))
+
+    def profile_end(self) -> dict:
+        pr = Profile()
+        _check(lib().phikron_batch_profile_end(self._h, C.byref(pr)))
+        return {"ms": dict(zip(KERNEL_CLASSES, list(pr.ms))),
+                "launches": dict(zip(KERNEL_CLASSES, list(pr.launches))),
+                "timed_launches": pr.timed_launches}
+
     def check_status(self):
         _check(lib().phikron_batch_check_status(self._h))
 
@@ -401,6 +416,17 @@ class Integrator:
         _check(lib().phikron_erk_get_info(self._h, C.byref(inf)))
         return {k: (list(getattr(inf, k)) if k in ("c", "s", "m", "actions") else getattr(inf, k))
                 for k, _ in ErkInfo._fields_}
+
+    def profile_begin(self, max_timed: int = 0):
+        """Count (and, if max_timed > 0, event-time) the kernels of the following steps."""
+        _check(lib().phikron_erk_profile_begin(self._h, max_timed))
+
+    def profile_end(self) -> dict:
+        pr = Profile()
+        _check(lib().phikron_erk_profile_end(self._h, C.byref(pr)))
+        return {"ms": dict(zip(KERNEL_CLASSES, list(pr.ms))),
+                "launches": dict(zip(KERNEL_CLASSES, list(pr.launches))),
+                "timed_launches": pr.timed_launches}
 
     def check_status(self):
         _check(lib().phikron_erk_check_status(self._h))
