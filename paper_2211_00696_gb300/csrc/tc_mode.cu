@@ -491,6 +491,26 @@ __device__ __forceinline__ void ws_load(const WsSlot& S, int orow, int kc, Raw<I
 }
 
 
+// Fastest-axis float-float passes: the raw values of chunk kc of a producer warp, loaded so that
+// one load instruction covers two full 256-byte chunk rows (lane = 16-byte piece q = lane & 15
+// of row 16 w + 2 j + lane / 16, j = 0..7): whole 32-byte sectors per request, where one row per
+// lane and 16 bytes per request left half of every sector unused.  Piece j lands in
+// raw[j / 4].f[2 (j % 4)] and .f[2 (j % 4) + 1] (values k = kc + 2q and kc + 2q + 1).
+__device__ __forceinline__ void ws_load_rows(const WsSlot& S, int w, int lane, int kc, Raw<false>* raw) {
+  const int q = lane & 15;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const long long gr = S.g0 + 16 * w + 2 * j + (lane >> 4);
+    const int k = kc + 2 * q;
+    const bool ok = gr < S.B0 && k < S.n;   // n is a multiple of 16: k + 1 < n as well
+    const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(S.in) +
+                                                                gr * (long long)S.n + k))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    raw[j >> 2].f[2 * (j & 3)] = make_float2(v.x, v.y);
+    raw[j >> 2].f[2 * (j & 3) + 1] = make_float2(v.z, v.w);
+  }
+}
+
 template <int KS, bool IN_F64, bool TRANS>
 __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
   const unsigned long long wl = P.wait_ns;  // limit of every bounded wait
@@ -545,6 +565,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
     // ------------------------------------------------------------ producers
     const int orow = tid & 127;
     const int kh = tid >> 7;  // k-groups 2*kh, 2*kh + 1 of every 32-wide chunk
+    // fastest-axis float-float passes load and cut by row pieces (ws_load_rows)
+    constexpr bool ROWS = !TRANS && !IN_F64;
     uint32_t it = 0, tc = 0;
     int e_last = -1;          // thread 0: chunk of the latest E bulk copy
     long long tile = blockIdx.x;
@@ -556,8 +578,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       if (!have) {
         ws_fail(abort_s, status);
       } else {
-        ws_load<IN_F64, TRANS>(S, orow, 16 * kh, raw[0]);
-        ws_load<IN_F64, TRANS>(S, orow, 16 * kh + 8, raw[1]);
+        if constexpr (ROWS) {
+          ws_load_rows(S, warp, lane, 0, raw);
+        } else {
+          ws_load<IN_F64, TRANS>(S, orow, 16 * kh, raw[0]);
+          ws_load<IN_F64, TRANS>(S, orow, 16 * kh + 8, raw[1]);
+        }
       }
     }
     for (; have && tile < total_tiles; tile += gridDim.x, ++tc) {
@@ -574,12 +600,20 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
         // their latency overlaps the wait and this chunk's cutting
         Raw<IN_F64> rawn[2];
         if (c + 1 < nchunks) {
-          ws_load<IN_F64, TRANS>(S, orow, 32 * (c + 1) + 16 * kh, rawn[0]);
-          ws_load<IN_F64, TRANS>(S, orow, 32 * (c + 1) + 16 * kh + 8, rawn[1]);
+          if constexpr (ROWS) {
+            ws_load_rows(S, warp, lane, 32 * (c + 1), rawn);
+          } else {
+            ws_load<IN_F64, TRANS>(S, orow, 32 * (c + 1) + 16 * kh, rawn[0]);
+            ws_load<IN_F64, TRANS>(S, orow, 32 * (c + 1) + 16 * kh + 8, rawn[1]);
+          }
         } else if (has_next) {
           if (ws_get(slots, slot_full, slot_empty, tc + 1, Sn, wl)) {
-            ws_load<IN_F64, TRANS>(Sn, orow, 16 * kh, rawn[0]);
-            ws_load<IN_F64, TRANS>(Sn, orow, 16 * kh + 8, rawn[1]);
+            if constexpr (ROWS) {
+              ws_load_rows(Sn, warp, lane, 0, rawn);
+            } else {
+              ws_load<IN_F64, TRANS>(Sn, orow, 16 * kh, rawn[0]);
+              ws_load<IN_F64, TRANS>(Sn, orow, 16 * kh + 8, rawn[1]);
+            }
           } else {
             ws_fail(abort_s, status);
           }
@@ -591,6 +625,21 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
           mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)HALF_BYTES);
           bulk_copy_g2s(smem_u32(sE), S.ebase + (size_t)c * HALF_BYTES, (uint32_t)HALF_BYTES, smem_u32(&full_e[st]));
         }
+        if constexpr (ROWS) {
+          // piece j: values k = 2q, 2q + 1 of row 16 w + 2 j + lane / 16 -> 4 bytes of every slice
+          const int q = lane & 15;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float2 a = raw[j >> 2].f[2 * (j & 3)], b = raw[j >> 2].f[2 * (j & 3) + 1];
+            float2 v[KS];
+            cut_ff_float2<KS>(make_float2(a.x, b.x), make_float2(a.y, b.y), xsc, v);
+            const int r = 16 * warp + 2 * j + (lane >> 4);
+            const uint32_t off = chunk_offset(r, q >> 2) + (uint32_t)(q & 3) * 4u;
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl)
+              *reinterpret_cast<uint32_t*>(sX + sl * SLICE_BYTES + off) = pack_bf16x2(v[sl].x, v[sl].y);
+          }
+        } else {
 #pragma unroll
         for (int g2 = 0; g2 < 2; ++g2) {
           uint32_t pk[KS][4];
@@ -616,6 +665,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
 #pragma unroll
           for (int sl = 0; sl < KS; ++sl)
             *reinterpret_cast<uint4*>(sX + sl * SLICE_BYTES + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+        }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(smem_u32(&full_x[st]));
