@@ -94,17 +94,6 @@ __device__ __forceinline__ bool fw_get(const FwSlot* slots, uint64_t* slot_full,
   return ok;
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
-      : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -229,8 +218,10 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
 
   if (warp < FW_EPI0) {
     // ------------------------------------------------------------ producers
-    const int f = tid >> 2;    // fiber of the tile
-    const int kq = tid & 3;    // K values 8 kq .. 8 kq + 7 of every 32-wide chunk
+    // a load instruction covers two fibers' 256-byte chunk rows (lane = 16-byte piece q of fiber
+    // 8 w + 2 j + lane / 16, j = 0..3): consecutive shared-memory addresses, where one fiber per
+    // four lanes put every lane of a warp on the same two bank groups
+    const int q = lane & 15;   // K values 2q, 2q + 1 of every 32-wide chunk
     uint32_t sc = 0, it = 0;
     int e_last = -1;           // thread 0: chunk of the latest E bulk copy
     bool stop = false;
@@ -243,8 +234,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
           ws_fail(abort_s, status);
         if (__any_sync(0xffffffffu, *abort_s)) { stop = true; break; }   // warp-uniform
         const float xsc = pow2f_full(-S.eX);
-        const float2* raw = reinterpret_cast<const float2*>(rawbuf + r * FW_RAW) + (long long)f * S.n;
-        const bool vf = f < S.nfib;
+        const float2* raw = reinterpret_cast<const float2*>(rawbuf + r * FW_RAW);
         for (int c = 0; c < S.nsub; ++c, ++it) {
           const uint32_t st = it % NST, use = it / NST;
           uint8_t* sX = smem + st * STAGE;
@@ -256,26 +246,24 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
             bulk_copy_g2s(smem_u32(sX + XBYTES), S.ebase + (size_t)c * KS * SLICE_BYTES, (uint32_t)(KS * SLICE_BYTES),
                           smem_u32(&full_e[st]));
           }
-          const int k0 = c * KC + 8 * kq;
+          const int k = c * KC + 2 * q;   // n is a multiple of 16: k < n covers k + 1
           float4 v[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) v[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (vf && k0 < S.n) {  // n is a multiple of 16: k0 < n covers k0 .. k0 + 7
-#pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = *reinterpret_cast<const float4*>(raw + k0 + 2 * e);
+          for (int j = 0; j < 4; ++j) {
+            const int f = 8 * warp + 2 * j + (lane >> 4);
+            v[j] = (f < S.nfib && k < S.n) ? *reinterpret_cast<const float4*>(raw + (long long)f * S.n + k)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          uint32_t pk[KS][4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
+          for (int j = 0; j < 4; ++j) {
             float2 a[KS];
-            cut_ff_float2<KS>(make_float2(v[e].x, v[e].z), make_float2(v[e].y, v[e].w), xsc, a);
+            cut_ff_float2<KS>(make_float2(v[j].x, v[j].z), make_float2(v[j].y, v[j].w), xsc, a);
+            const int f = 8 * warp + 2 * j + (lane >> 4);
+            const uint32_t off = chunk_offset(f, q >> 2) + (uint32_t)(q & 3) * 4u;
 #pragma unroll
-            for (int sl = 0; sl < KS; ++sl) pk[sl][e] = pack_bf16x2(a[sl].x, a[sl].y);
+            for (int sl = 0; sl < KS; ++sl)
+              *reinterpret_cast<uint32_t*>(sX + sl * FW_XSL + off) = pack_bf16x2(a[sl].x, a[sl].y);
           }
-          const uint32_t off = chunk_offset(f, kq);
-#pragma unroll
-          for (int sl = 0; sl < KS; ++sl)
-            *reinterpret_cast<uint4*>(sX + sl * FW_XSL + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_arrive_warp(smem_u32(&full_x[st]), lane);
         }
