@@ -41,6 +41,8 @@ extern "C" {
 #define PHIKRON_ETIMEOUT       -4  /* a bounded device wait gave up (device status word)        */
 #define PHIKRON_ENOTCONVERGED  -5  /* planner root finding failed (Theorem 3.2 quartic)         */
 #define PHIKRON_ENOTSUP        -6  /* option combination not built                              */
+#define PHIKRON_EBOUNDS        -7  /* bounds-checked build: a kernel access fell outside every
+                                      registered device range (see phikron_checked_violation)  */
 
 /* Largest number of Kronecker factors (dimensions) a plan accepts. */
 #define PHIKRON_MAX_DIMS 6
@@ -354,6 +356,30 @@ const char* phikron_last_error(void);
  * buffer allocations after the first k (counted from when the variable took that value) are
  * refused and the call returns PHIKRON_ENOMEM; unset it to allocate normally. */
 long long phikron_live_device_buffers(void);
+
+/* ------------------------------------------------------------------ bounds-checked build
+ * libphikron_checked.so is the same library compiled with PHIKRON_CHECKED (the binding loads
+ * it when the environment variable PHIKRON_CHECKED is 1).  There, every global load, store,
+ * atomic and bulk copy of the apply-path kernels (mode products on both paths, the fused
+ * node-weight pass, the elementwise float-float and float64 kernels, the integrators' and the
+ * plan-time kernels) first checks that its byte range lies inside a registered device range:
+ * an allocation of the library, or a buffer the caller passed to the call being run (each
+ * entry point registers its caller buffers on its stream before its kernels, so one call at a
+ * time per process).  An access outside is skipped (loads read zeros, a bulk copy reads a
+ * block of zeros, stores and atomics are dropped) and recorded; nothing traps.  With a
+ * violation recorded, phikron_check_status (and the batch and integrator variants) return
+ * PHIKRON_EBOUNDS.  The checks are slow (a linear scan of the ranges per access): a tool for
+ * small cases, not for timing.  PHIKRON_CHECKED_SHRINK = k (test hook) registers every library
+ * allocation k bytes short, so that accesses to the last k bytes of real allocations are
+ * refused and recorded without any access outside memory the library owns.
+ *
+ * phikron_checked: 1 in the checked build, 0 in the default one.
+ * phikron_checked_violation (HOST): the first recorded violation since the last read (site
+ *   0 = none; its address and size) and the number of violations; clears the record.
+ * phikron_checked_site_name (HOST): text of a site number. */
+int phikron_checked(void);
+int phikron_checked_violation(int* site, unsigned long long* addr, unsigned long long* bytes, int* count);
+const char* phikron_checked_site_name(int site);
 
 /* ------------------------------------------------------------------ planner (host only)
  * Algorithms 3-5 of Sec. 3.2-3.3, exposed so the planner can be checked without a GPU.

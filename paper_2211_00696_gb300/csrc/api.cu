@@ -11,8 +11,11 @@
 #include <string>
 #include <vector>
 
+#include "checked.cuh"
 #include "common.h"
 #include "plan.h"
+
+PK_CHK_BIND(api)
 
 namespace phikron {
 
@@ -104,6 +107,7 @@ std::atomic<long long> g_live_buffers{0};
 
 void device_free(void* p) {
   if (!p) return;
+  chk::remove(p);
   cudaFree(p);
   g_live_buffers.fetch_sub(1);
 }
@@ -124,6 +128,7 @@ int device_malloc(void** p, size_t bytes, const char* who) {
     return PHIKRON_ENOMEM;
   }
   g_live_buffers.fetch_add(1);
+  chk::add(*p, bytes);
   return PHIKRON_OK;
 }
 
@@ -524,8 +529,8 @@ __global__ void cc_err_kernel(const double* __restrict__ Y, const double* __rest
   for (int j = 0; j < p; ++j) {
     double dmax = 0.0, ymax = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-      const double y = Y[(size_t)j * N + i];
-      dmax = fmax(dmax, fabs(y - Yo[(size_t)j * N + i]));
+      const double y = chk::ld_ck(Y + (size_t)j * N + i, chk::SITE_PLAN);
+      dmax = fmax(dmax, fabs(y - chk::ld_ck(Yo + (size_t)j * N + i, chk::SITE_PLAN)));
       ymax = fmax(ymax, fabs(y));
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -533,8 +538,10 @@ __global__ void cc_err_kernel(const double* __restrict__ Y, const double* __rest
       ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
     }
     if ((threadIdx.x & 31) == 0) {
-      atomicMax(slots + 2 * j, (unsigned long long)__double_as_longlong(dmax));
-      atomicMax(slots + 2 * j + 1, (unsigned long long)__double_as_longlong(ymax));
+      if (PK_CK(slots + 2 * j, 2 * sizeof(unsigned long long), chk::SITE_PLAN)) {
+        atomicMax(slots + 2 * j, (unsigned long long)__double_as_longlong(dmax));
+        atomicMax(slots + 2 * j + 1, (unsigned long long)__double_as_longlong(ymax));
+      }
     }
   }
 }
@@ -746,6 +753,11 @@ int phikron_plan(phikron_plan_t* out, int dims, const double* const* A, const in
   return PHIKRON_OK;
 }
 
+// bytes of the Out buffer of nrhs applies: (l_max+1) vectors per rhs, twice with half_step
+static size_t apply_out_bytes(const Plan& P, int nrhs) {
+  return sizeof(double) * (size_t)P.N * (size_t)(P.p + 1) * (P.opts.half_step ? 2 : 1) * (size_t)nrhs;
+}
+
 int phikron_apply(phikron_plan_t plan, const double* V, double* Out, void* stream) {
   clear_error();
   if (!plan || !V || !Out) { set_error("phikron_apply: NULL argument"); return PHIKRON_EINVAL; }
@@ -753,6 +765,9 @@ int phikron_apply(phikron_plan_t plan, const double* V, double* Out, void* strea
   DeviceGuard dg(P.opts.device);
   if (dg.rc != PHIKRON_OK) return dg.rc;
   ProfScope ps(&P.prof);
+  const chk::Range r[2] = {{V, sizeof(double) * (size_t)P.N}, {Out, apply_out_bytes(P, 1)}};
+  chk::CallScope cs(static_cast<cudaStream_t>(stream), r, 2);
+  PK_RET(cs.rc);
   return apply_dispatch(P, 1, V, Out, static_cast<cudaStream_t>(stream));
 }
 
@@ -764,6 +779,9 @@ int phikron_apply_many(phikron_plan_t plan, int nrhs, const double* V, double* O
   DeviceGuard dg(P.opts.device);
   if (dg.rc != PHIKRON_OK) return dg.rc;
   ProfScope ps(&P.prof);
+  const chk::Range r[2] = {{V, sizeof(double) * (size_t)P.N * nrhs}, {Out, apply_out_bytes(P, nrhs)}};
+  chk::CallScope cs(static_cast<cudaStream_t>(stream), r, 2);
+  PK_RET(cs.rc);
   return apply_dispatch(P, nrhs, V, Out, static_cast<cudaStream_t>(stream));
 }
 
@@ -783,6 +801,9 @@ int phikron_apply_combo(phikron_plan_t plan, const double* B, double* Out, void*
   DeviceGuard dg(P.opts.device);
   if (dg.rc != PHIKRON_OK) return dg.rc;
   ProfScope ps(&P.prof);
+  const chk::Range r[2] = {{B, sizeof(double) * (size_t)P.N * P.p}, {Out, sizeof(double) * (size_t)P.N}};
+  chk::CallScope cs(static_cast<cudaStream_t>(stream), r, 2);
+  PK_RET(cs.rc);
   return apply_combo_f64(P, B, Out, static_cast<cudaStream_t>(stream));
 }
 
@@ -791,6 +812,8 @@ int phikron_apply_combo(phikron_plan_t plan, const double* B, double* Out, void*
 // copied out on another, so that both link directions and the GPU are busy at once.
 // Events order each reuse of a staging buffer after the work that last touched it.
 static int host_many_enqueue(Plan& P, const double* V_host, double* Out_host, int count, cudaStream_t st) {
+  chk::CallScope cs(st, nullptr, 0);   // device work on the plan's own staging buffers only
+  PK_RET(cs.rc);
   const size_t in_elems = (size_t)P.N;
   const size_t out_elems = (size_t)P.N * (P.p + 1) * (P.opts.half_step ? 2 : 1);
   if (!P.dV2) {
@@ -928,6 +951,7 @@ int phikron_check_status(phikron_plan_t plan) {
   DeviceGuard dg(plan->impl.opts.device);
   if (dg.rc != PHIKRON_OK) return dg.rc;
   PK_TRY_CUDA(cudaDeviceSynchronize());
+  PK_RET(chk::status());   // bounds-checked build: a recorded out-of-range access
   int st = 0;
   PK_RET(mixed_status(plan->impl, &st));
   if (st != 0) {
@@ -1021,6 +1045,10 @@ int phikron_expm_batched(int count, int n, const double* A, const double* scale,
     }
     norms1 = own.data();
   }
+  const size_t mats = sizeof(double) * (size_t)n * n * (size_t)std::max(count, 0);
+  const chk::Range r[3] = {{A, mats}, {E, mats}, {workspace, expm_workspace_bytes(count, n)}};
+  chk::CallScope cs(st, r, 3);
+  PK_RET(cs.rc);
   return expm_batched(count, n, A, scale, norms1, E, workspace, st);
 }
 
@@ -1046,6 +1074,13 @@ int phikron_kron_apply_f64(int dims, const int* n, const double* const* E, const
     return PHIKRON_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  chk::Range r[PHIKRON_MAX_DIMS + 3];
+  for (int d = 0; d < dims; ++d) r[d] = {E[d], sizeof(double) * (size_t)n[d] * n[d]};
+  r[dims] = {V, sizeof(double) * (size_t)N};
+  r[dims + 1] = {Out, sizeof(double) * (size_t)N};
+  r[dims + 2] = {work, sizeof(double) * (size_t)N};
+  chk::CallScope cs(st, r, dims + 3);
+  PK_RET(cs.rc);
   const double* cur = V;
   for (int d = 0; d < dims; ++d) {
     long long B0 = 1, R = 1;

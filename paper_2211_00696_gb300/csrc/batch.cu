@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "batch.h"
+#include "checked.cuh"
 #include "plan.h"
 
 using namespace phikron;
@@ -210,6 +211,17 @@ int phikron_batch_apply(phikron_batch_t b, const double* const* V, double* const
   }
   if (b->device >= 0 && b->device != prev) cudaSetDevice(b->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<chk::Range> rr;
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    const Plan& P = *b->plans[i];
+    rr.push_back({V[i], sizeof(double) * (size_t)P.N * b->nrhs});
+    rr.push_back({Out[i], sizeof(double) * (size_t)P.N * (P.p + 1) * (b->half ? 2 : 1) * b->nrhs});
+  }
+  chk::CallScope cs(st, rr.data(), (int)rr.size());
+  if (cs.rc != PHIKRON_OK) {
+    if (b->device >= 0 && b->device != prev) cudaSetDevice(prev);
+    return cs.rc;
+  }
   const PtrArgs args = make_args(*b, V, Out);
   int rc = PHIKRON_OK;
   if (!b->tuned) {
@@ -298,6 +310,7 @@ int phikron_batch_check_status(phikron_batch_t b) {
     return PHIKRON_EINVAL;
   }
   PK_TRY_CUDA(cudaDeviceSynchronize());
+  PK_RET(chk::status());   // bounds-checked build: a recorded out-of-range access
   for (auto& s : b->cand) {
     int st = 0;
     PK_RET(seq_status(*s, &st));

@@ -20,8 +20,11 @@
 #include <new>
 #include <vector>
 
+#include "checked.cuh"
 #include "common.h"
 #include "profile.h"
+
+PK_CHK_BIND(erk)
 
 namespace phikron {
 namespace {
@@ -53,10 +56,13 @@ __global__ void __launch_bounds__(EW) kron_csr_kernel(KronCsr K, const double* _
       rest /= nd;
       const long long base = idx - (long long)i * stride;
       const Csr c = K.f[d];
-      for (int q = c.rowptr[i]; q < c.rowptr[i + 1]; ++q) acc = fma(c.val[q], u[base + (long long)c.col[q] * stride], acc);
+      const int q0 = chk::ld_ck(c.rowptr + i, chk::SITE_ERK), q1 = chk::ld_ck(c.rowptr + i + 1, chk::SITE_ERK);
+      for (int q = q0; q < q1; ++q)
+        acc = fma(chk::ld_ck(c.val + q, chk::SITE_ERK),
+                  chk::ld_ck(u + base + (long long)chk::ld_ck(c.col + q, chk::SITE_ERK) * stride, chk::SITE_ERK), acc);
       stride *= nd;
     }
-    Au[idx] = acc;
+    chk::st_ck(Au + idx, acc, chk::SITE_ERK);
   }
 }
 
@@ -65,12 +71,12 @@ __global__ void __launch_bounds__(EW) residual_kernel(int nonlin, const double* 
                                                      const double* __restrict__ Au, const double* __restrict__ S,
                                                      double* __restrict__ D, long long N) {
   for (long long i = blockIdx.x * (long long)EW + threadIdx.x; i < N; i += (long long)gridDim.x * EW) {
-    const double x = U[i];
+    const double x = chk::ld_ck(U + i, chk::SITE_ERK);
     double f = 0.0;
     if (nonlin == PHIKRON_NONLIN_ALLEN_CAHN) f = x - x * x * x;
-    double d = f - Au[i];
-    if (S) d -= S[i];
-    D[i] = d;
+    double d = f - chk::ld_ck(Au + i, chk::SITE_ERK);
+    if (S) d -= chk::ld_ck(S + i, chk::SITE_ERK);
+    chk::st_ck(D + i, d, chk::SITE_ERK);
   }
 }
 
@@ -83,9 +89,9 @@ struct Comb {
 
 __global__ void __launch_bounds__(EW) combine_kernel(const double* base, Comb cb, double* out, long long N) {
   for (long long i = blockIdx.x * (long long)EW + threadIdx.x; i < N; i += (long long)gridDim.x * EW) {
-    double v = base ? base[i] : 0.0;
-    for (int k = 0; k < cb.nx; ++k) v = fma(cb.c[k], cb.X[k][i], v);
-    out[i] = v;
+    double v = base ? chk::ld_ck(base + i, chk::SITE_ERK) : 0.0;
+    for (int k = 0; k < cb.nx; ++k) v = fma(cb.c[k], chk::ld_ck(cb.X[k] + i, chk::SITE_ERK), v);
+    chk::st_ck(out + i, v, chk::SITE_ERK);
   }
 }
 
@@ -304,6 +310,9 @@ int phikron_erk_step(phikron_erk_t erk, double* U, int nsteps, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = PHIKRON_OK;
   ProfScope ps(&erk->prof);
+  const chk::Range r[1] = {{U, sizeof(double) * (size_t)erk->N}};
+  chk::CallScope cs(st, r, 1);
+  rc = cs.rc;
   for (int k = 0; k < nsteps && rc == PHIKRON_OK; ++k) rc = erk_step(*erk, U, st);
   if (erk->device >= 0 && erk->device != prev) cudaSetDevice(prev);
   return rc;

@@ -19,7 +19,10 @@
 #include <cmath>
 #include <vector>
 
+#include "checked.cuh"
 #include "common.h"
+
+PK_CHK_BIND(expm)
 
 namespace phikron {
 
@@ -43,7 +46,7 @@ __global__ void scale_batch_kernel(const double* __restrict__ in, double* __rest
   const long long ioff = (long long)sc.src[bl] * nn;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
        i += (long long)gridDim.x * blockDim.x)
-    out[off + i] = sc.s[bl] * in[ioff + i];
+    chk::st_ck(out + off + i, sc.s[bl] * chk::ld_ck(in + ioff + i, chk::SITE_PLAN), chk::SITE_PLAN);
 }
 
 // out = c0*X0 + c1*X1 + c2*X2 + c3*X3 + cI*I  (batched; null X with zero coefficient skipped)
@@ -55,13 +58,13 @@ __global__ void lincomb_kernel(double* __restrict__ out, const double* __restric
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     double v = 0.0;
-    if (X0) v = fma(c0, X0[e], v);
-    if (X1) v = fma(c1, X1[e], v);
-    if (X2) v = fma(c2, X2[e], v);
-    if (X3) v = fma(c3, X3[e], v);
+    if (X0) v = fma(c0, chk::ld_ck(X0 + e, chk::SITE_PLAN), v);
+    if (X1) v = fma(c1, chk::ld_ck(X1 + e, chk::SITE_PLAN), v);
+    if (X2) v = fma(c2, chk::ld_ck(X2 + e, chk::SITE_PLAN), v);
+    if (X3) v = fma(c3, chk::ld_ck(X3 + e, chk::SITE_PLAN), v);
     const long long w = e % nn;
     if ((w / n) == (w % n)) v += cI;
-    out[e] = v;
+    chk::st_ck(out + e, v, chk::SITE_PLAN);
   }
 }
 

@@ -35,10 +35,13 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "checked.cuh"
 #include "common.h"
 #include "mixed.h"
 #include "profile.h"
 #include "tc_common.cuh"
+
+PK_CHK_BIND(fused)
 
 namespace phikron {
 namespace tc {
@@ -94,6 +97,15 @@ __device__ __forceinline__ bool fw_get(const FwSlot* slots, uint64_t* slot_full,
   return ok;
 }
 
+using chk::st_ck;
+
+// pointer-table entry plus offset, or the direct pointer
+__device__ __forceinline__ void* fw_tab(const FPass& P, int tab, long long off, void* direct) {
+  if (tab < 0) return direct;
+  if (!PK_CK(P.ptrtab + tab, sizeof(void*), chk::SITE_TABLE)) return nullptr;
+  return (void*)((char*)P.ptrtab[tab] + off);
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -136,11 +148,11 @@ __device__ __forceinline__ void fw_write_out(uint32_t sums, int nvec, int ch, bo
         for (int q = 0; q < 8; ++q) {
           if (8 * g + q < nfib) {
             const long long e = o + (long long)q * n;
-            if (yff) yff[e] = make_float2(h[q], l[q]);
+            if (yff) st_ck(yff + e, make_float2(h[q], l[q]), chk::SITE_FUSED_STORE);
             if (y64 || y2) {
               const double d = ff::to_f64(h[q], l[q]);
-              if (y64) y64[e] = d;
-              if (y2) y2[e] = d;
+              if (y64) st_ck(y64 + e, d, chk::SITE_FUSED_STORE);
+              if (y2) st_ck(y2 + e, d, chk::SITE_FUSED_STORE);
             }
             mx = max(mx, __float_as_uint(h[q]) & 0x7FFFFFFFu);
           }
@@ -152,7 +164,8 @@ __device__ __forceinline__ void fw_write_out(uint32_t sums, int nvec, int ch, bo
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       // |y| < 2^{biased - 126}; a zero output keeps the slot's initial (very negative) value
       const int emax = (int)(mx >> 23);
-      if (lane == 0 && emax > 0) atomicMax(out_exp + v, emax - 126);
+      if (lane == 0 && emax > 0 && PK_CK(out_exp + v, sizeof(int), chk::SITE_FUSED_STORE))
+        atomicMax(out_exp + v, emax - 126);
     }
   }
 }
@@ -183,6 +196,12 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long total_tiles = P.total_tiles;
+#ifdef PHIKRON_CHECKED
+  // a launch whose tables are not registered does nothing (uniform over the CTA)
+  if (!PK_CK(P.jobs, sizeof(FJob) * (size_t)P.njobs, chk::SITE_TABLE) ||
+      (P.ptrtab && !PK_CK(P.ptrtab, sizeof(void*) * MAX_PTRS, chk::SITE_TABLE)))
+    return;
+#endif
   const unsigned long long wl = P.wait_ns;
   if (tid == 0) {
     for (int q = 0; q < NST; ++q) {
@@ -243,7 +262,9 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
           if (tid == 0) {
             e_last = (int)it;
             mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)(KS * SLICE_BYTES));
-            bulk_copy_g2s(smem_u32(sX + XBYTES), S.ebase + (size_t)c * KS * SLICE_BYTES, (uint32_t)(KS * SLICE_BYTES),
+            bulk_copy_g2s(smem_u32(sX + XBYTES),
+                          PK_CK_SRC(S.ebase + (size_t)c * KS * SLICE_BYTES, KS * SLICE_BYTES, chk::SITE_FUSED_ECOPY),
+                          (uint32_t)(KS * SLICE_BYTES),
                           smem_u32(&full_e[st]));
           }
           const int k = c * KC + 2 * q;   // n is a multiple of 16: k < n covers k + 1
@@ -295,7 +316,8 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
         if (epi_vote_any256(!ok || *abort_s)) { stop = true; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const bool vi = i < S.n;
-        const float scl = pow2f(S.eX + (vi ? __ldg(S.rexp + i) : 0));
+        const float scl =
+            pow2f(S.eX + ((vi && PK_CK(S.rexp + i, sizeof(int), chk::SITE_FUSED_READ)) ? __ldg(S.rexp + i) : 0));
         const float2 sc2 = make_float2(scl, scl);
         const bool direct = (S.flags & FW_DIRECT) != 0;
         const bool first = (S.flags & FW_FIRST) != 0;
@@ -375,8 +397,8 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
           fw_write_out(sums, 1, ch, vi, i, lane, S.n, S.nfib, 0, nullptr, S.dout, nullptr, nullptr);
         } else if (S.flags & FW_LAST) {
           const FJob& J = P.jobs[S.job];
-          void* o = J.out_tab >= 0 ? (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out) : J.out;
-          void* o2 = J.out2_tab >= 0 ? (void*)((char*)P.ptrtab[J.out2_tab] + J.tab_off_out2) : J.out2;
+          void* o = fw_tab(P, J.out_tab, J.tab_off_out, J.out);
+          void* o2 = fw_tab(P, J.out2_tab, J.tab_off_out2, J.out2);
           const long long t0 = S.f0 * (long long)S.n;
           float2* yff = J.out_f64 ? nullptr : reinterpret_cast<float2*>(o) + t0;
           double* y64 = J.out_f64 ? reinterpret_cast<double*>(o) + t0 : nullptr;
@@ -456,6 +478,11 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
         if (sc >= FW_SLOTS && !mbar_wait(smem_u32(&slot_empty[q]), ((sc / FW_SLOTS) - 1) & 1u, wl))
           ws_fail(abort_s, status);
         if (*abort_s) { stop = true; break; }
+        if (!PK_CK(P.nodes + J.node0 + nd, sizeof(FNode), chk::SITE_TABLE)) {
+          ws_fail(abort_s, status);   // no node to run: the CTA stops like on an expired wait
+          stop = true;
+          break;
+        }
         const FNode& N = P.nodes[J.node0 + nd];
         FwSlot& S = slots[q];
         S.xsrc = N.in + f0 * J.n;
@@ -465,14 +492,16 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
         int flags = 0;
         if (N.direct) {
           flags |= FW_DIRECT;
-          double* o = reinterpret_cast<double*>(N.out_tab >= 0 ? (void*)((char*)P.ptrtab[N.out_tab] + N.tab_off_out)
-                                                                : N.out);
+          double* o = reinterpret_cast<double*>(fw_tab(P, N.out_tab, N.tab_off_out, N.out));
           S.dout = o + f0 * J.n;
         } else {
           if (N.k == 0) flags |= FW_FIRST;
           if (N.k == J.m - 1) flags |= FW_LAST;
 #pragma unroll
-          for (int j = 0; j < P_; ++j) S.c[j] = J.coef[j * J.m + N.k];
+          for (int j = 0; j < P_; ++j) {
+            const float2* cp = J.coef + j * J.m + N.k;
+            S.c[j] = PK_CK(cp, sizeof(float2), chk::SITE_FUSED_READ) ? *cp : make_float2(0.f, 0.f);
+          }
         }
         if (nd == J.nnodes - 1) flags |= FW_END;
         S.flags = flags;
@@ -481,7 +510,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
         S.nsub = (J.n + KC - 1) / KC;
         S.nfib = nfib;
         S.xbytes = (unsigned)(nfib * J.n * 8);
-        const int eX = *N.in_exp;
+        const int eX = PK_CK(N.in_exp, sizeof(int), chk::SITE_FUSED_READ) ? *N.in_exp : -1000;
         S.eX = eX < -600 ? 0 : eX;  // all-zero input
         S.job = job;
         mbar_arrive(smem_u32(&slot_full[q]));
@@ -490,7 +519,8 @@ __global__ void __launch_bounds__(FW_THREADS, 1) fused_weights_kernel(const __gr
         if (u >= 1 && !mbar_wait(smem_u32(&raw_empty[r]), (u - 1) & 1u, wl)) ws_fail(abort_s, status);
         if (*abort_s) { stop = true; break; }
         mbar_expect_tx(smem_u32(&raw_full[r]), S.xbytes);
-        bulk_copy_g2s(smem_u32(rawbuf + r * FW_RAW), S.xsrc, S.xbytes, smem_u32(&raw_full[r]));
+        bulk_copy_g2s(smem_u32(rawbuf + r * FW_RAW), PK_CK_SRC(S.xsrc, S.xbytes, chk::SITE_FUSED_XCOPY), S.xbytes,
+                      smem_u32(&raw_full[r]));
         r_last = sc;
       }
     }

@@ -8,12 +8,18 @@
 // (arithmetic intensity 8 flop per staged byte against a pipe that needs < 1).
 #include <cstdio>
 
+#include "checked.cuh"
 #include "common.h"
 #include "profile.h"
+
+PK_CHK_BIND(gemm_f64)
 
 namespace phikron {
 
 namespace {
+
+using chk::ld_ck;
+using chk::st_ck;
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
@@ -46,11 +52,11 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g, int tiles_n, lo
       int ii, kk;
       if (a_k_fast) { ii = e / BK; kk = e % BK; } else { kk = e / BM; ii = e % BM; }
       const int gi = m0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < g.M && gk < g.K) ? A[gi * g.sAm + gk * g.sAk] : 0.0;
+      As[kk][ii] = (gi < g.M && gk < g.K) ? ld_ck(A + gi * g.sAm + gk * g.sAk, chk::SITE_F64_LOAD) : 0.0;
       int jj, kb;
       if (b_n_fast) { kb = e / BN; jj = e % BN; } else { jj = e / BK; kb = e % BK; }
       const int gj = n0 + jj, gkb = k0 + kb;
-      Bs[kb][jj] = (gj < g.N && gkb < g.K) ? B[gkb * g.sBk + gj * g.sBn] : 0.0;
+      Bs[kb][jj] = (gj < g.N && gkb < g.K) ? ld_ck(B + gkb * g.sBk + gj * g.sBn, chk::SITE_F64_LOAD) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g, int tiles_n, lo
       if (gj >= g.N) continue;
       double* c = C + gi * g.sCm + gj * g.sCn;
       const double v = g.alpha * acc[i][j];
-      *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
+      if (PK_CK(c, sizeof(double), chk::SITE_F64_STORE)) *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
     }
   }
 }
@@ -91,14 +97,14 @@ __global__ void weighted_sum_kernel(const double* __restrict__ T, long long T_st
 #pragma unroll
     for (int j = 0; j < 20; ++j) acc[j] = 0.0;
     for (int k = 0; k < m; ++k) {
-      const double t = T[k * T_stride + i];
+      const double t = ld_ck(T + k * T_stride + i, chk::SITE_F64_LOAD);
 #pragma unroll
       for (int j = 0; j < 20; ++j)
-        if (j < p) acc[j] = fma(coef[j * m + k], t, acc[j]);
+        if (j < p) acc[j] = fma(ld_ck(coef + j * m + k, chk::SITE_F64_LOAD), t, acc[j]);
     }
 #pragma unroll
     for (int j = 0; j < 20; ++j)
-      if (j < p) Y[j * Y_stride + i] = acc[j];
+      if (j < p) st_ck(Y + j * Y_stride + i, acc[j], chk::SITE_F64_STORE);
   }
 }
 
@@ -115,15 +121,15 @@ __global__ void squaring_combine_kernel(const double* __restrict__ Z, const doub
     double y[20];
 #pragma unroll
     for (int j = 0; j < 20; ++j)
-      if (j < p) y[j] = Y[j * stride + i];
+      if (j < p) y[j] = ld_ck(Y + j * stride + i, chk::SITE_F64_LOAD);
     double scale = 1.0;
 #pragma unroll
     for (int q = 1; q <= 20; ++q) {
       if (q > p) break;
       scale *= 0.5;
-      double acc = Z[(q - 1) * stride + i];
+      double acc = ld_ck(Z + (q - 1) * stride + i, chk::SITE_F64_LOAD);
       for (int j = 1; j <= q; ++j) acc = fma(y[j - 1], inv_factorial(q - j), acc);
-      Yn[(q - 1) * stride + i] = scale * acc;
+      st_ck(Yn + (q - 1) * stride + i, scale * acc, chk::SITE_F64_STORE);
     }
   }
 }

@@ -20,11 +20,27 @@
 #include "plan.h"
 #include "profile.h"
 #include "batch.h"
+#include "checked.cuh"
 #include "ff_arith.cuh"
+
+PK_CHK_BIND(mixed)
 
 namespace phikron {
 
 namespace {
+
+using chk::st_ck;
+
+// Bounds-checked build: a launch whose job table or pointer table is not registered does
+// nothing (every thread decides alike).
+#ifdef PHIKRON_CHECKED
+#define PK_CHECK_EW_TABLES(jobs, njobs, tab)                                                  \
+  if (!PK_CK((jobs), sizeof(EJob) * (size_t)(njobs), chk::SITE_TABLE) ||                        \
+      ((tab) && !PK_CK((tab), sizeof(void*) * MAX_PTRS, chk::SITE_TABLE)))                      \
+    return;
+#else
+#define PK_CHECK_EW_TABLES(jobs, njobs, tab)
+#endif
 
 constexpr int KC = 32;
 constexpr int SLICE_BYTES = 128 * KC * 2;
@@ -51,12 +67,15 @@ __device__ __forceinline__ int find_ejob(const EJob* jobs, int njobs, long long 
 }
 
 __device__ __forceinline__ void* tab_ptr(const void* const* tab, int e, long long off, void* direct) {
-  return e >= 0 ? (void*)((char*)tab[e] + off) : direct;
+  if (e < 0) return direct;
+  if (!PK_CK(tab + e, sizeof(void*), chk::SITE_TABLE)) return nullptr;
+  return (void*)((char*)tab[e] + off);
 }
 
 // two consecutive float-float values (16 bytes; every vector offset used is a multiple of 2)
 __device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
-  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 v = PK_CK(p, 16, chk::SITE_EW_LOAD) ? __ldg(reinterpret_cast<const float4*>(p))
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
   a = make_float2(v.x, v.y);
   b = make_float2(v.z, v.w);
 }
@@ -67,15 +86,16 @@ __device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
 __device__ __forceinline__ void st_pair(void* out, void* out2, bool f64, long long off, float2 a, float2 b, int& emax) {
   if (f64) {
     double* o = reinterpret_cast<double*>(out) + off;
-    o[0] = to_f64(a.x, a.y);
-    o[1] = to_f64(b.x, b.y);
+    st_ck(o, to_f64(a.x, a.y), chk::SITE_EW_STORE);
+    st_ck(o + 1, to_f64(b.x, b.y), chk::SITE_EW_STORE);
   } else {
-    *reinterpret_cast<float4*>(reinterpret_cast<float2*>(out) + off) = make_float4(a.x, a.y, b.x, b.y);
+    st_ck(reinterpret_cast<float4*>(reinterpret_cast<float2*>(out) + off), make_float4(a.x, a.y, b.x, b.y),
+          chk::SITE_EW_STORE);
   }
   if (out2) {
     double* o = reinterpret_cast<double*>(out2) + off;
-    o[0] = to_f64(a.x, a.y);
-    o[1] = to_f64(b.x, b.y);
+    st_ck(o, to_f64(a.x, a.y), chk::SITE_EW_STORE);
+    st_ck(o + 1, to_f64(b.x, b.y), chk::SITE_EW_STORE);
   }
   emax = max(emax, (int)((__float_as_uint(a.x) >> 23) & 0xFFu));
   emax = max(emax, (int)((__float_as_uint(b.x) >> 23) & 0xFFu));
@@ -101,7 +121,7 @@ __device__ __forceinline__ void block_exp_flush(int (&emax)[P_], int* out_exp, i
     int v = -1000;
 #pragma unroll
     for (int w = 0; w < EW_THREADS / 32; ++w) v = max(v, red[threadIdx.x][w]);
-    if (v > -1000) atomicMax(out_exp + threadIdx.x, v);
+    if (v > -1000 && PK_CK(out_exp + threadIdx.x, sizeof(int), chk::SITE_EW_EXP)) atomicMax(out_exp + threadIdx.x, v);
   }
   __syncthreads();
 }
@@ -116,6 +136,7 @@ __device__ __forceinline__ void block_exp_flush(int (&emax)[P_], int* out_exp, i
 template <int P_>
 __global__ void __launch_bounds__(EW_THREADS, P_ <= 3 ? 4 : (P_ <= 7 ? 3 : (P_ <= 11 ? 2 : 1)))
     g_weighted_kernel(const EJob* __restrict__ jobs, int njobs, long long total, const void* const* ptrtab) {
+  PK_CHECK_EW_TABLES(jobs, njobs, ptrtab);
   constexpr int KB = P_ <= 3 ? 6 : (P_ <= 8 ? 4 : 2);  // T_k per batch (register budget without spills)
   __shared__ float2 cs[P_ * MAXM];
   __shared__ int red[P_][EW_THREADS / 32];
@@ -128,7 +149,8 @@ __global__ void __launch_bounds__(EW_THREADS, P_ <= 3 ? 4 : (P_ <= 7 ? 3 : (P_ <
     const EJob& J = jobs[jb];
     if (jb != cur) {
       if (cur >= 0) block_exp_flush<P_>(emax, jobs[cur].out_exp, red);
-      for (int q = threadIdx.x; q < P_ * J.m; q += EW_THREADS) cs[q] = J.coef[q];
+      for (int q = threadIdx.x; q < P_ * J.m; q += EW_THREADS)
+        cs[q] = PK_CK(J.coef + q, sizeof(float2), chk::SITE_EW_LOAD) ? J.coef[q] : make_float2(0.f, 0.f);
       __syncthreads();
       cur = jb;
     }
@@ -175,6 +197,7 @@ template <int P_>
 __global__ void __launch_bounds__(EW_THREADS, P_ <= 6 ? 4 : (P_ <= 11 ? 2 : 1)) g_squaring_kernel(const EJob* __restrict__ jobs, int njobs,
                                                                    long long total, const void* const* ptrtab,
                                                                    InvFact inv) {
+  PK_CHECK_EW_TABLES(jobs, njobs, ptrtab);
   __shared__ int red[P_][EW_THREADS / 32];
   int emax[P_];
 #pragma unroll
@@ -232,6 +255,7 @@ __global__ void __launch_bounds__(EW_THREADS, P_ <= 6 ? 4 : (P_ <= 11 ? 2 : 1)) 
 // e with |v| < 2^e over a float64 vector (integer ops only), grouped over jobs
 __global__ void __launch_bounds__(EW_THREADS) g_expscan_kernel(const EJob* __restrict__ jobs, int njobs,
                                                                long long total, const void* const* ptrtab) {
+  PK_CHECK_EW_TABLES(jobs, njobs, ptrtab);
   __shared__ int red[1][EW_THREADS / 32];
   int emax[1] = {0};  // float64 exponent field: |v| < 2^{emax - 1022}
   int cur = -1;
@@ -248,7 +272,8 @@ __global__ void __launch_bounds__(EW_THREADS) g_expscan_kernel(const EJob* __res
 #pragma unroll
     for (int q = 0; q < 2 * EW_PAIRS; ++q) {
       const long long i = base + (long long)q * EW_THREADS + threadIdx.x;
-      b[q] = i < J.N ? (uint64_t)__double_as_longlong(__ldg(v + i)) : 0ull;
+      b[q] = (i < J.N && PK_CK(v + i, sizeof(double), chk::SITE_EW_LOAD)) ? (uint64_t)__double_as_longlong(__ldg(v + i))
+                                                                          : 0ull;
     }
 #pragma unroll
     for (int q = 0; q < 2 * EW_PAIRS; ++q) {
@@ -278,7 +303,7 @@ __global__ void pad_scatter_kernel(const double* __restrict__ V, double* __restr
       src += (long long)id * mul;
       mul *= D.n[d];
     }
-    Vp[q] = in ? V[src] : 0.0;
+    st_ck(Vp + q, (in && PK_CK(V + src, sizeof(double), chk::SITE_EW_LOAD)) ? V[src] : 0.0, chk::SITE_EW_STORE);
   }
 }
 
@@ -296,7 +321,8 @@ __global__ void pad_gather_kernel(const double* __restrict__ Op, double* __restr
       dst += (long long)id * mul;
       mul *= D.pn[d];
     }
-    Out[t] = Op[(long long)v * PN + dst];
+    const double* sp = Op + (long long)v * PN + dst;
+    st_ck(Out + t, PK_CK(sp, sizeof(double), chk::SITE_EW_LOAD) ? *sp : 0.0, chk::SITE_EW_STORE);
   }
 }
 

@@ -23,6 +23,7 @@
 // not overlap (PHIKRON_EINVAL).
 #include <mutex>
 
+#include "checked.cuh"
 #include "common.h"
 
 namespace phikron {
@@ -51,6 +52,7 @@ int scratch_address(double** out) {
       return PHIKRON_ECUDA;
     }
     g_scratch_dev[dev] = static_cast<double*>(p);
+    chk::add(p, sizeof(double) * kMaxElems);
   }
   *out = g_scratch_dev[dev];
   return PHIKRON_OK;
@@ -92,6 +94,12 @@ extern "C" int phikron_kron_apply_f64_noalloc(int dims, const int* n, const doub
   double* work = nullptr;
   PK_RET(scratch_address(&work));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  chk::Range r[PHIKRON_MAX_DIMS + 2];
+  for (int d = 0; d < dims; ++d) r[d] = {E[d], sizeof(double) * (size_t)n[d] * n[d]};
+  r[dims] = {V, sizeof(double) * (size_t)N};
+  r[dims + 1] = {Out, sizeof(double) * (size_t)N};
+  chk::CallScope cs(st, r, dims + 2);
+  PK_RET(cs.rc);
   const double* cur = V;
   for (int d = 0; d < dims; ++d) {
     long long B0 = 1, R = 1;

@@ -46,10 +46,13 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "checked.cuh"
 #include "common.h"
 #include "mixed.h"
 #include "profile.h"
 #include "tc_common.cuh"
+
+PK_CHK_BIND(tc_mode)
 
 namespace phikron {
 namespace tc {
@@ -57,6 +60,42 @@ namespace tc {
 namespace {
 
 constexpr int NTHREADS = 512;
+
+// Bounds-checked build: a launch whose job table or pointer table is not registered does
+// nothing (every thread of the CTA decides alike, before any barrier or TMEM allocation).
+#ifdef PHIKRON_CHECKED
+#define PK_CHECK_TABLES(P)                                                                  \
+  if (!PK_CK((P).jobs, sizeof(GJob) * (size_t)(P).njobs, chk::SITE_TABLE) ||                  \
+      ((P).ptrtab && !PK_CK((P).ptrtab, sizeof(void*) * MAX_PTRS, chk::SITE_TABLE)))          \
+    return;
+#else
+#define PK_CHECK_TABLES(P)
+#endif
+
+using chk::st_ck;
+
+// input / output base of a job: direct, or a pointer-table entry plus offset
+__device__ __forceinline__ const void* job_in(const GPass& P, const GJob& J) {
+  if (J.in_tab < 0) return J.in;
+  if (!PK_CK(P.ptrtab + J.in_tab, sizeof(void*), chk::SITE_TABLE)) return nullptr;
+  return (const void*)((const char*)P.ptrtab[J.in_tab] + J.tab_off_in);
+}
+
+__device__ __forceinline__ void* job_out(const GPass& P, const GJob& J) {
+  if (J.out_tab < 0) return J.out;
+  if (!PK_CK(P.ptrtab + J.out_tab, sizeof(void*), chk::SITE_TABLE)) return nullptr;
+  return (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out);
+}
+
+// exponent of a job's input (all-zero input: 0)
+__device__ __forceinline__ int job_in_exp(const GJob& J) {
+  const int eX = PK_CK(J.in_exp, sizeof(int), chk::SITE_MODE_EXP) ? *J.in_exp : -1000;
+  return eX < -600 ? 0 : eX;
+}
+
+__device__ __forceinline__ void out_exp_max(int* out_exp, int v) {
+  if (out_exp && PK_CK(out_exp, sizeof(int), chk::SITE_MODE_EXP)) atomicMax(out_exp, v);
+}
 
 // Raw operand values of one thread for one 32-wide K sub-chunk: 8 consecutive k of its row.
 template <bool IN_F64>
@@ -108,13 +147,12 @@ __device__ __forceinline__ TileCtx tile_ctx(const GPass& P, long long tile, int 
   } else {
     t.row0 = th * 128;
   }
-  int eX = *J.in_exp;
-  t.eX = eX < -600 ? 0 : eX;  // all-zero input
+  t.eX = job_in_exp(J);
   t.in_base = TRANS ? t.b0 * (long long)J.n * J.R : 0;
   t.gr = TRANS ? t.r0 + orow : t.row0 + orow;
   t.valid_row = TRANS ? (t.gr < J.R) : (t.gr < J.B0);
-  t.in = (J.in_tab >= 0) ? (const void*)((const char*)P.ptrtab[J.in_tab] + J.tab_off_in) : J.in;
-  t.out = (J.out_tab >= 0) ? (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out) : J.out;
+  t.in = job_in(P, J);
+  t.out = job_out(P, J);
   return t;
 }
 
@@ -123,8 +161,8 @@ __device__ __forceinline__ void load_raw(const TileCtx& t, int sub, int kq, Raw<
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int k = sub * 32 + kq * 8 + e;
-    const bool ok = t.valid_row && k < t.n;
     const long long idx = TRANS ? t.in_base + (long long)k * t.R + t.gr : t.gr * (long long)t.n + k;
+    const bool ok = t.valid_row && k < t.n && PK_CK((const char*)t.in + 8 * idx, 8, chk::SITE_MODE_LOAD);
     if (IN_F64)
       raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(t.in) + idx) : 0.0;
     else
@@ -136,6 +174,7 @@ __device__ __forceinline__ void load_raw(const TileCtx& t, int sub, int kq, Raw<
 // accumulated over the full contraction K = n in chunks of 32*SUB.
 template <int KS, int SUB, bool IN_F64, bool TRANS>
 __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant__ GPass P, int* status) {
+  PK_CHECK_TABLES(P);
   const unsigned long long wl = P.wait_ns;  // limit of every bounded wait
   extern __shared__ __align__(1024) uint8_t smem[];
   // [stage 0: X slices SUB*KS*8K | E slices SUB*KS*8K][stage 1: ...][mbarriers][scales][tmem]
@@ -185,7 +224,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
     const int nrows_e = min(128, n - 128 * T.rb);   // E rows in this row block
     const uint8_t* ebase = J.eslices + (size_t)T.rb * (size_t)T.nsub * KS * SLICE_BYTES;
     if (tid < 128) {
-      const int E = T.eX + ((tid < nrows_e) ? J.rexp[T.rb * 128 + tid] : 0);
+      const int* rx = J.rexp + T.rb * 128 + tid;
+      const int E = T.eX + ((tid < nrows_e && PK_CK(rx, sizeof(int), chk::SITE_MODE_REXP)) ? *rx : 0);
       scale_s[tid] = pow2f(E);
     }
     const uint32_t idesc = TRANS ? make_idesc(128, nrows_e) : make_idesc(128, 128);
@@ -208,7 +248,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
       if (tid == 0) {  // E slices of this chunk: one asynchronous bulk copy ([sub][slice][8 KB])
         const uint32_t bytes = (uint32_t)(nsub_c * KS * SLICE_BYTES);
         mbar_expect_tx(smem_u32(&mbar_e[st]), bytes);
-        bulk_copy_g2s(smem_u32(sE), ebase + (size_t)c * SUB * KS * SLICE_BYTES, bytes, smem_u32(&mbar_e[st]));
+        bulk_copy_g2s(smem_u32(sE), PK_CK_SRC(ebase + (size_t)c * SUB * KS * SLICE_BYTES, bytes, chk::SITE_MODE_ECOPY),
+                      bytes, smem_u32(&mbar_e[st]));
         e_issued = it;
       }
       // raw values of the next chunk (or of the next tile's first chunk) go in flight now
@@ -360,16 +401,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) mode_kernel(const __grid_constant
           hi *= sc;
           lo *= sc;
           if (J.out_f64)
-            outF64[oidx] = ff_to_f64(hi, lo);
+            st_ck(outF64 + oidx, ff_to_f64(hi, lo), chk::SITE_MODE_STORE);
           else
-            outFF[oidx] = make_float2(hi, lo);
+            st_ck(outFF + oidx, make_float2(hi, lo), chk::SITE_MODE_STORE);
           emax = max(emax, (int)((__float_as_uint(hi) >> 23) & 0xFFu));
         }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
       // |v| < 2^{biased - 126}; a zero vector keeps the slot's initial (very negative) value
-      if (lane == 0 && J.out_exp && emax > 0) atomicMax(J.out_exp, emax - 126);
+      if (lane == 0 && emax > 0) out_exp_max(J.out_exp, emax - 126);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -469,10 +510,9 @@ __device__ __forceinline__ void ws_load(const WsSlot& S, int orow, int kc, Raw<I
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
       const int k = kc + e;
-      const bool ok = vr && k < S.n;
-      const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(S.in) +
-                                                                   gr * (long long)S.n + k))
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float2* src = reinterpret_cast<const float2*>(S.in) + gr * (long long)S.n + k;
+      const bool ok = vr && k < S.n && PK_CK(src, 16, chk::SITE_MODE_LOAD);
+      const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
       raw.f[e] = make_float2(v.x, v.y);
       raw.f[e + 1] = make_float2(v.z, v.w);
     }
@@ -481,8 +521,8 @@ __device__ __forceinline__ void ws_load(const WsSlot& S, int orow, int kc, Raw<I
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int k = kc + e;
-    const bool ok = vr && k < S.n;
     const long long idx = TRANS ? S.base + (long long)k * S.R + gr : gr * (long long)S.n + k;
+    const bool ok = vr && k < S.n && PK_CK((const char*)S.in + 8 * idx, 8, chk::SITE_MODE_LOAD);
     if (IN_F64)
       raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(S.in) + idx) : 0.0;
     else
@@ -502,10 +542,10 @@ __device__ __forceinline__ void ws_load_rows(const WsSlot& S, int w, int lane, i
   for (int j = 0; j < 8; ++j) {
     const long long gr = S.g0 + 16 * w + 2 * j + (lane >> 4);
     const int k = kc + 2 * q;
-    const bool ok = gr < S.B0 && k < S.n;   // n is a multiple of 16: k + 1 < n as well
-    const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(S.in) +
-                                                                gr * (long long)S.n + k))
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2* src = reinterpret_cast<const float2*>(S.in) + gr * (long long)S.n + k;
+    // n is a multiple of 16: k + 1 < n as well
+    const bool ok = gr < S.B0 && k < S.n && PK_CK(src, 16, chk::SITE_MODE_LOAD);
+    const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
     raw[j >> 2].f[2 * (j & 3)] = make_float2(v.x, v.y);
     raw[j >> 2].f[2 * (j & 3) + 1] = make_float2(v.z, v.w);
   }
@@ -513,6 +553,7 @@ __device__ __forceinline__ void ws_load_rows(const WsSlot& S, int w, int lane, i
 
 template <int KS, bool IN_F64, bool TRANS>
 __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
+  PK_CHECK_TABLES(P);
   const unsigned long long wl = P.wait_ns;  // limit of every bounded wait
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int HALF_BYTES = KS * SLICE_BYTES;
@@ -623,7 +664,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
         if (tid == 0) {
           e_last = (int)it;
           mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)HALF_BYTES);
-          bulk_copy_g2s(smem_u32(sE), S.ebase + (size_t)c * HALF_BYTES, (uint32_t)HALF_BYTES, smem_u32(&full_e[st]));
+          bulk_copy_g2s(smem_u32(sE), PK_CK_SRC(S.ebase + (size_t)c * HALF_BYTES, HALF_BYTES, chk::SITE_MODE_ECOPY),
+                        (uint32_t)HALF_BYTES, smem_u32(&full_e[st]));
         }
         if constexpr (ROWS) {
           // piece j: values k = 2q, 2q + 1 of row 16 w + 2 j + lane / 16 -> 4 bytes of every slice
@@ -689,7 +731,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       WsSlot S;
       bool ok = ws_get(slots, slot_full, slot_empty, tc, S, wl);
       asm volatile("bar.sync 1, 128;" ::: "memory");  // the previous tile's scale table is no longer read
-      if (ok) scale_s[et] = pow2f(S.eX + ((et < S.nrows_e) ? S.rexp[et] : 0));
+      if (ok)
+        scale_s[et] = pow2f(S.eX + ((et < S.nrows_e && PK_CK(S.rexp + et, sizeof(int), chk::SITE_MODE_REXP))
+                                        ? S.rexp[et] : 0));
       ok = ok && mbar_wait(smem_u32(tmem_full), tc & 1u, wl);
       if (!ok) ws_fail(abort_s, status);
       // the vote is also the barrier after the scale writes; every epilogue thread decides alike
@@ -721,8 +765,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
               const float2 sc = *reinterpret_cast<const float2*>(scale_s + cc + j);
               hi = mul2(hi, sc);
               lo = mul2(lo, sc);
-              dst[(long long)j * S.R] = make_float2(hi.x, lo.x);
-              dst[(long long)(j + 1) * S.R] = make_float2(hi.y, lo.y);
+              st_ck(dst + (long long)j * S.R, make_float2(hi.x, lo.x), chk::SITE_MODE_STORE);
+              st_ck(dst + (long long)(j + 1) * S.R, make_float2(hi.y, lo.y), chk::SITE_MODE_STORE);
               mxf = fmaxf(mxf, fmaxf(fabsf(hi.x), fabsf(hi.y)));
             }
           } else if (vg) {
@@ -736,8 +780,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
               const float2 sc = *reinterpret_cast<const float2*>(scale_s + cc + j);
               hi = mul2(hi, sc);
               lo = mul2(lo, sc);
-              dst[(long long)j * S.R] = ff_to_f64(hi.x, lo.x);
-              dst[(long long)(j + 1) * S.R] = ff_to_f64(hi.y, lo.y);
+              st_ck(dst + (long long)j * S.R, ff_to_f64(hi.x, lo.x), chk::SITE_MODE_STORE);
+              st_ck(dst + (long long)(j + 1) * S.R, ff_to_f64(hi.y, lo.y), chk::SITE_MODE_STORE);
               mxf = fmaxf(mxf, fmaxf(fabsf(hi.x), fabsf(hi.y)));
             }
           }
@@ -767,11 +811,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
               hi = mul2(hi, make_float2(sc, sc));
               lo = mul2(lo, make_float2(sc, sc));
               if (j < jn) {
-                dst[(long long)j * S.n] = make_float2(hi.x, lo.x);
+                st_ck(dst + (long long)j * S.n, make_float2(hi.x, lo.x), chk::SITE_MODE_STORE);
                 mxf = fmaxf(mxf, fabsf(hi.x));
               }
               if (j + 1 < jn) {
-                dst[(long long)(j + 1) * S.n] = make_float2(hi.y, lo.y);
+                st_ck(dst + (long long)(j + 1) * S.n, make_float2(hi.y, lo.y), chk::SITE_MODE_STORE);
                 mxf = fmaxf(mxf, fabsf(hi.y));
               }
             }
@@ -786,11 +830,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
               hi = mul2(hi, make_float2(sc, sc));
               lo = mul2(lo, make_float2(sc, sc));
               if (j < jn) {
-                dst[(long long)j * S.n] = ff_to_f64(hi.x, lo.x);
+                st_ck(dst + (long long)j * S.n, ff_to_f64(hi.x, lo.x), chk::SITE_MODE_STORE);
                 mxf = fmaxf(mxf, fabsf(hi.x));
               }
               if (j + 1 < jn) {
-                dst[(long long)(j + 1) * S.n] = ff_to_f64(hi.y, lo.y);
+                st_ck(dst + (long long)(j + 1) * S.n, ff_to_f64(hi.y, lo.y), chk::SITE_MODE_STORE);
                 mxf = fmaxf(mxf, fabsf(hi.y));
               }
             }
@@ -804,7 +848,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       // |v| < 2^{biased - 126}; a zero vector keeps the slot's initial (very negative) value
       const int emax = (int)(mx >> 23);
-      if (lane == 0 && S.out_exp && emax > 0) atomicMax(S.out_exp, emax - 126);
+      if (lane == 0 && emax > 0) out_exp_max(S.out_exp, emax - 126);
     }
   } else if (warp == WS_MMA || warp == WS_MMA2) {
     if (lane == 0) {
@@ -874,8 +918,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       const int rb = (int)(tj / per_rb);
       const long long th = tj % per_rb;
       WsSlot& S = slots[q];
-      S.in = (J.in_tab >= 0) ? (const void*)((const char*)P.ptrtab[J.in_tab] + J.tab_off_in) : J.in;
-      S.out = (J.out_tab >= 0) ? (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out) : J.out;
+      S.in = job_in(P, J);
+      S.out = job_out(P, J);
       const int nsub = (J.n + 31) / 32;
       S.ebase = J.eslices + (size_t)rb * (size_t)nsub * KS * SLICE_BYTES;
       S.rexp = J.rexp + 128 * rb;
@@ -887,8 +931,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       S.n = J.n;
       S.nsub = nsub;
       S.rb = rb;
-      const int eX = *J.in_exp;
-      S.eX = eX < -600 ? 0 : eX;  // all-zero input
+      S.eX = job_in_exp(J);
       S.nrows_e = min(128, J.n - 128 * rb);
       S.out_f64 = J.out_f64;
       mbar_arrive(smem_u32(&slot_full[q]));
@@ -930,10 +973,9 @@ __device__ __forceinline__ void db_load(const WsSlot& S, int fib, int kc, Raw<IN
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
       const int k = kc + e;
-      const bool ok = vr && k < S.n;
-      const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(S.in) +
-                                                                   gr * (long long)S.n + k))
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float2* src = reinterpret_cast<const float2*>(S.in) + gr * (long long)S.n + k;
+      const bool ok = vr && k < S.n && PK_CK(src, 16, chk::SITE_MODE_LOAD);
+      const float4 v = ok ? __ldg(reinterpret_cast<const float4*>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
       raw.f[e] = make_float2(v.x, v.y);
       raw.f[e + 1] = make_float2(v.z, v.w);
     }
@@ -942,8 +984,8 @@ __device__ __forceinline__ void db_load(const WsSlot& S, int fib, int kc, Raw<IN
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int k = kc + e;
-    const bool ok = vr && k < S.n;
     const long long idx = TRANS ? S.base + (long long)k * S.R + gr : gr * (long long)S.n + k;
+    const bool ok = vr && k < S.n && PK_CK((const char*)S.in + 8 * idx, 8, chk::SITE_MODE_LOAD);
     if (IN_F64)
       raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(S.in) + idx) : 0.0;
     else
@@ -953,6 +995,7 @@ __device__ __forceinline__ void db_load(const WsSlot& S, int fib, int kc, Raw<IN
 
 template <int KS, bool IN_F64, bool TRANS>
 __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_constant__ GPass P, int* status) {
+  PK_CHECK_TABLES(P);
   const unsigned long long wl = P.wait_ns;  // limit of every bounded wait
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int XBYTES = KS * DB_XSLICE;
@@ -1047,8 +1090,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
         if (tid == 0) {
           e_last = (int)it;
           mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)(KS * SLICE_BYTES));
-          bulk_copy_g2s(smem_u32(sE), S.ebase + (size_t)c * KS * SLICE_BYTES, (uint32_t)(KS * SLICE_BYTES),
-                        smem_u32(&full_e[st]));
+          bulk_copy_g2s(smem_u32(sE),
+                        PK_CK_SRC(S.ebase + (size_t)c * KS * SLICE_BYTES, KS * SLICE_BYTES, chk::SITE_MODE_ECOPY),
+                        (uint32_t)(KS * SLICE_BYTES), smem_u32(&full_e[st]));
         }
         uint32_t pk[KS][4];
 #pragma unroll
@@ -1102,7 +1146,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t tb = tmem + 256u * b + ((uint32_t)(q4 * 32) << 16);
       const bool vi = i < S.nrows_e;
-      const float sc = pow2f(S.eX + (vi ? __ldg(S.rexp + i) : 0));
+      const float sc = pow2f(S.eX + ((vi && PK_CK(S.rexp + i, sizeof(int), chk::SITE_MODE_REXP)) ? __ldg(S.rexp + i) : 0));
       const int ncols = TRANS ? (int)min(64LL, S.R - S.g0) : (int)min(64LL, S.B0 - S.g0);
       const bool f64 = S.out_f64 != 0;
       uint32_t mx = 0;
@@ -1149,12 +1193,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
             float2* dst = reinterpret_cast<float2*>(S.out) + o;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              if (j < jn) dst[(long long)j * S.n] = make_float2(hs[j], ls[j]);
+              if (j < jn) st_ck(dst + (long long)j * S.n, make_float2(hs[j], ls[j]), chk::SITE_MODE_STORE);
           } else {
             double* dst = reinterpret_cast<double*>(S.out) + o;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              if (j < jn) dst[(long long)j * S.n] = ff_to_f64(hs[j], ls[j]);
+              if (j < jn) st_ck(dst + (long long)j * S.n, ff_to_f64(hs[j], ls[j]), chk::SITE_MODE_STORE);
           }
         }
       }
@@ -1171,13 +1215,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
             const long long o = S.base + (long long)(128 * S.rb + r) * S.R + S.g0 + c2;
             const uint8_t* src = staging + r * DB_STAGE_PITCH + c2 * 8;
             if (!f64) {
-              *reinterpret_cast<float4*>(reinterpret_cast<float2*>(S.out) + o) = *reinterpret_cast<const float4*>(src);
+              st_ck(reinterpret_cast<float4*>(reinterpret_cast<float2*>(S.out) + o), *reinterpret_cast<const float4*>(src),
+                    chk::SITE_MODE_STORE);
             } else {
               // the caller's float64 buffer need only be 8-byte aligned
               const double2 v = *reinterpret_cast<const double2*>(src);
               double* dst = reinterpret_cast<double*>(S.out) + o;
-              dst[0] = v.x;
-              dst[1] = v.y;
+              st_ck(dst, v.x, chk::SITE_MODE_STORE);
+              st_ck(dst + 1, v.y, chk::SITE_MODE_STORE);
             }
           }
         }
@@ -1186,7 +1231,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       // |v| < 2^{biased - 126}; a zero vector keeps the slot's initial (very negative) value
       const int emax = (int)(mx >> 23);
-      if (lane == 0 && S.out_exp && emax > 0) atomicMax(S.out_exp, emax - 126);
+      if (lane == 0 && emax > 0) out_exp_max(S.out_exp, emax - 126);
     }
   } else if (warp == WS_MMA || warp == WS_MMA2) {
     if (lane == 0) {
@@ -1255,8 +1300,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       const int rb = (int)(tj / per_rb);
       const long long th = tj % per_rb;
       WsSlot& S = slots[q];
-      S.in = (J.in_tab >= 0) ? (const void*)((const char*)P.ptrtab[J.in_tab] + J.tab_off_in) : J.in;
-      S.out = (J.out_tab >= 0) ? (void*)((char*)P.ptrtab[J.out_tab] + J.tab_off_out) : J.out;
+      S.in = job_in(P, J);
+      S.out = job_out(P, J);
       const int nsub = (J.n + 31) / 32;
       S.ebase = J.eslices + (size_t)rb * (size_t)nsub * KS * SLICE_BYTES;
       S.rexp = J.rexp + 128 * rb;
@@ -1268,8 +1313,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       S.n = J.n;
       S.nsub = nsub;
       S.rb = rb;
-      const int eX = *J.in_exp;
-      S.eX = eX < -600 ? 0 : eX;  // all-zero input
+      S.eX = job_in_exp(J);
       S.nrows_e = min(128, J.n - 128 * rb);
       S.out_f64 = J.out_f64;
       mbar_arrive(smem_u32(&slot_full[q]));
@@ -1282,7 +1326,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
 
 __global__ void ptrtab_set_kernel(void** tab, PtrArgs args) {
   const int i = threadIdx.x;
-  if (i < args.n) tab[i] = args.p[i];
+  if (i < args.n) st_ck(tab + i, args.p[i], chk::SITE_TABLE);
 }
 
 }  // namespace

@@ -13,16 +13,18 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libphikron.so")
+# the bounds-checked build (every kernel access range-checked; slow) when PHIKRON_CHECKED is 1
+CHECKED = os.environ.get("PHIKRON_CHECKED") == "1"
+LIB_PATH = os.path.join(HERE, "libphikron_checked.so" if CHECKED else "libphikron.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONVERGED, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONVERGED, ENOTSUP, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 QUAD_GAUSS, QUAD_CC, QUAD_CC_ADAPTIVE = 0, 1, 2
 PREC_FP64, PREC_OZAKI_BF16 = 0, 2
 SELECT_PAPER, SELECT_MLP = 0, 1
 SELECTOR_USED = {0: "algorithm5", 1: "network", 2: "network+m", 3: "fallback"}
 
 _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
-             ENOTCONVERGED: "ENOTCONVERGED", ENOTSUP: "ENOTSUP"}
+             ENOTCONVERGED: "ENOTCONVERGED", ENOTSUP: "ENOTSUP", EBOUNDS: "EBOUNDS"}
 
 
 class PhikronError(RuntimeError):
@@ -128,17 +130,22 @@ SIGNATURES = {
     "phikron_kron_apply_f64": (C.c_int, [C.c_int, _IP, C.POINTER(C.c_void_p), C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "phikron_noalloc_max_elements": (C.c_longlong, []),
+    "phikron_checked": (C.c_int, []),
+    "phikron_checked_violation": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_ulonglong),
+                                            C.POINTER(C.c_ulonglong), C.POINTER(C.c_int)]),
+    "phikron_checked_site_name": (C.c_char_p, [C.c_int]),
     "phikron_kron_apply_f64_noalloc": (C.c_int, [C.c_int, _IP, C.POINTER(C.c_void_p), C.c_void_p,
                                                  C.c_void_p, C.c_void_p]),
 }
 
 
 def lib():
-    """Loads libphikron.so (raises if it is absent: build it with paper_2211_00696_gb300.build)."""
+    """Loads libphikron.so (libphikron_checked.so with PHIKRON_CHECKED=1; raises if it is
+    absent: build it with paper_2211_00696_gb300.build)."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError(f"libphikron.so not built at {LIB_PATH}; run "
+            raise ImportError(f"{os.path.basename(LIB_PATH)} not built at {LIB_PATH}; run "
                               "`python -m paper_2211_00696_gb300.build`")
         L = C.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
@@ -470,3 +477,14 @@ def kron_apply_f64(mats, V, stream=None):
     _check(lib().phikron_kron_apply_f64(len(mats), ns, ptrs, V.data_ptr(), out.data_ptr(),
                                         work.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+def checked_violation() -> dict:
+    """The bounds-checked build's first recorded out-of-range access since the last read
+    (site 0: none) and the number of them; reading clears the record."""
+    site, cnt = C.c_int(), C.c_int()
+    addr, nb = C.c_ulonglong(), C.c_ulonglong()
+    _check(lib().phikron_checked_violation(C.byref(site), C.byref(addr), C.byref(nb), C.byref(cnt)))
+    return {"site": site.value, "name": lib().phikron_checked_site_name(site.value).decode(),
+            "addr": addr.value, "bytes": nb.value, "count": cnt.value}
+

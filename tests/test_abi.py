@@ -32,6 +32,30 @@ def test_library_exports_every_declared_symbol():
     assert declared <= set(B.SIGNATURES), declared - set(B.SIGNATURES)
 
 
+def test_checked_library_exports_every_declared_symbol():
+    """The bounds-checked variant (built by the same build step) exports the same C ABI and
+    reports itself; its record reads empty without any device work."""
+    import ctypes as C
+    from paper_2211_00696_gb300 import build as BLD
+    path = BLD.CHECKED.lib
+    assert os.path.exists(path), path
+    L = C.CDLL(path)
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+    L.phikron_checked.restype = C.c_int
+    assert L.phikron_checked() == 1
+    assert pk.lib().phikron_checked() == 0
+    site, cnt = C.c_int(-1), C.c_int(-1)
+    addr, nb = C.c_ulonglong(1), C.c_ulonglong(1)
+    for lib in (L, pk.lib()):
+        assert lib.phikron_checked_violation(C.byref(site), C.byref(addr), C.byref(nb), C.byref(cnt)) == 0
+        assert (site.value, cnt.value, addr.value, nb.value) == (0, 0, 0, 0)
+    L.phikron_checked_site_name.restype = C.c_char_p
+    assert L.phikron_checked_site_name(1) == b"mode kernel operand load"
+    assert L.phikron_checked_site_name(17) == b"plan-time kernel"
+    assert L.phikron_checked_site_name(18) == b"unknown"
+
+
 def test_planner_matches_oracle_exactly():
     for alpha in (0.37, 2.0, 8.712, 27.7092, 384.0, 1331.2, 85196.8, 3.1e5):
         for tol in (1e-6, 1e-8, 1e-10, 1e-14):
