@@ -169,6 +169,7 @@ int phikron_batch_create(phikron_batch_t* out, int count, const phikron_plan_t* 
             c.ws = var >= 1;
             c.db = var == 2;
             c.fuse = fused_weights_default();
+            c.rr = raw_ring_default();
             cfgs.push_back(c);
             if (!autotune) break;
           }

@@ -21,6 +21,7 @@ struct Step {
   long long total;   // tiles (mode) or blocks (elementwise)
   int p;
   PassShape shape;
+  long long tmap_off = -1;   // raw-ring mode pass: first tensor map (index) in Seq::dTmaps
 };
 
 struct Seq {
@@ -29,6 +30,7 @@ struct Seq {
   EJob* dE = nullptr;
   FJob* dF = nullptr;      // fused node passes: jobs and their nodes
   FNode* dFN = nullptr;
+  uint8_t* dTmaps = nullptr;   // TMA tensor maps of the raw-ring passes' inputs (128 B each)
   bool fused = false;      // the node phase ends in a fused weighted pass
   int* dSlots = nullptr;
   int nslots = 0;
@@ -60,6 +62,7 @@ struct SeqConfig {
   bool ws = true;         // warp-specialised mode kernel
   bool db = false;        // double-buffered 128 x 64-tile mode kernel where every n >= 64
   bool fuse = true;       // fold Algorithm 1's weights into the last node pass where it applies
+  bool rr = true;         // raw-ring warp-specialised kernel where it applies
 };
 
 struct MixedView {
@@ -79,6 +82,8 @@ bool mode_kernel_db_default();
 // Fused node-weight pass where it applies if the environment variable PHIKRON_FUSED_WEIGHTS is
 // "1" (measured slower than the separate passes on the 128^3 workload; see fused.cu).
 bool fused_weights_default();
+// Raw-ring mode kernel where it applies, unless PHIKRON_RAW_RING is "0".
+bool raw_ring_default();
 
 const MixedView mixed_view(const Plan& P, int d);
 int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& cfg);

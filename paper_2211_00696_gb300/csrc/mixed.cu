@@ -595,6 +595,7 @@ int precision_setup(Plan& P) {
   cfg.ws = mode_kernel_ws_default();
   cfg.db = mode_kernel_db_default();
   cfg.fuse = fused_weights_default();
+  cfg.rr = raw_ring_default();
   PK_RET(seq_build(M->seq, units, 1, cfg));
   return PHIKRON_OK;
 }
@@ -677,6 +678,7 @@ struct Builder {
   std::vector<Step> steps;
   int nslots = 0;
   bool big_first = false;
+  std::vector<uint8_t> tmaps;   // tensor maps of the raw-ring passes' inputs
 
   void mode_step(std::vector<GJob> jobs, const PassShape& shape) {
     if (jobs.empty()) return;
@@ -758,6 +760,11 @@ bool mode_kernel_db_default() {
 bool fused_weights_default() {
   const char* v = std::getenv("PHIKRON_FUSED_WEIGHTS");
   return v && std::strcmp(v, "1") == 0;
+}
+
+bool raw_ring_default() {
+  const char* v = std::getenv("PHIKRON_RAW_RING");
+  return !(v && std::strcmp(v, "0") == 0);
 }
 
 int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& cfg) {
@@ -917,9 +924,28 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       int minn = 1 << 30;
       for (const GJob& j : jobs) minn = std::min(minn, j.n);
       sh.db = cfg.db && minn >= 64;
+      // the raw ring's bulk copies read float-float inputs through direct, 16-byte aligned
+      // pointers (the library's own buffers), in runs whose lengths and offsets are multiples
+      // of 16 bytes: n (and R on transposed passes) multiples of 16
+      bool direct16 = true;
+      for (const GJob& j : jobs)
+        direct16 = direct16 && j.in_tab < 0 && (reinterpret_cast<uintptr_t>(j.in) & 15u) == 0 && j.n % 16 == 0 &&
+                   (!trans || j.R % 16 == 0);
+      sh.rr = cfg.rr && cfg.ws && !sh.in_f64 && cfg.slices <= 4 && direct16;
       if (dims == 1) sh.trans = false;
       // all jobs of one pass share the formulation (same axis d)
       B.mode_step(jobs, sh);
+      if (sh.rr) {
+        Step& stp = B.steps.back();
+        const size_t off = B.tmaps.size();
+        B.tmaps.resize(off + 128 * (size_t)stp.count);
+        if (tc::encode_raw_maps(B.gjobs.data() + stp.off, stp.count, sh.trans, B.tmaps.data() + off) == PHIKRON_OK) {
+          stp.tmap_off = (long long)(off / 128);
+        } else {   // no tensor maps: the register-loading kernel
+          B.tmaps.resize(off);
+          stp.shape.rr = false;
+        }
+      }
       for (size_t q = 0; q < vs.size(); ++q)
         if (newslot[q] >= 0) cur[q] = newslot[q];
     }
@@ -1106,6 +1132,10 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
   PK_RET(seq_alloc(S, (void**)&S.dE, sizeof(EJob) * std::max<size_t>(1, B.ejobs.size())));
   PK_RET(seq_alloc(S, (void**)&S.dF, sizeof(FJob) * std::max<size_t>(1, B.fjobs.size())));
   PK_RET(seq_alloc(S, (void**)&S.dFN, sizeof(FNode) * std::max<size_t>(1, B.fnodes.size())));
+  if (!B.tmaps.empty()) {
+    PK_RET(seq_alloc(S, (void**)&S.dTmaps, B.tmaps.size()));
+    PK_TRY_CUDA(cudaMemcpy(S.dTmaps, B.tmaps.data(), B.tmaps.size(), cudaMemcpyHostToDevice));
+  }
   if (!B.fjobs.empty())
     PK_TRY_CUDA(cudaMemcpy(S.dF, B.fjobs.data(), sizeof(FJob) * B.fjobs.size(), cudaMemcpyHostToDevice));
   if (!B.fnodes.empty())
@@ -1148,6 +1178,7 @@ int seq_launch_all(Seq& S, cudaStream_t st) {
       P.total_tiles = s.total;
       P.ptrtab = S.dPtrtab;
       P.wait_ns = S.wait_ns;
+      P.tmaps = (s.tmap_off >= 0) ? S.dTmaps + 128 * s.tmap_off : nullptr;
       PK_RET(tc::mode_pass(P, s.shape, S.dStatus, st));
     } else if (s.kind == STEP_FUSED) {
       FPass F;

@@ -31,6 +31,7 @@ struct GPass {
   long long total_tiles;
   const void* const* ptrtab;
   unsigned long long wait_ns;  // limit of every bounded mbarrier wait (wall clock)
+  const void* tmaps;       // raw-ring passes: one 128-byte TMA tensor map per job (its input)
 };
 
 struct PassShape {
@@ -40,6 +41,8 @@ struct PassShape {
   bool in_f64, trans;
   bool ws;                 // warp-specialised kernel (producer / MMA / epilogue warps)
   bool db;                 // double-buffered 128 x 64 tiles (needs n >= 64 in every job)
+  bool rr;                 // warp-specialised kernel with the raw ring (float-float input,
+                           // <= 4 slices, every job's input 16-byte aligned and direct)
 };
 
 // Shared-memory operand layout of one 128-row x 32-K BF16 slice (8 KiB), K-major, used by the
@@ -60,6 +63,8 @@ struct PtrArgs {
 namespace tc {
 int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st);
 int set_ptrtab(void** tab, const PtrArgs& args, cudaStream_t st);
+// TMA tensor maps (128 bytes each, job order) of the inputs of a raw-ring mode pass's jobs
+int encode_raw_maps(const GJob* jobs, int njobs, bool trans, uint8_t* out);
 size_t smem_bytes(int ks, int sub);
 }  // namespace tc
 

@@ -45,6 +45,9 @@
 // status word, waits (bounded) for its own tensor-core work, frees its TMEM and returns.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+
+#include <cuda.h>
 
 #include "checked.cuh"
 #include "common.h"
@@ -488,6 +491,22 @@ size_t ws_smem_bytes(int ks) {
   return (size_t)ws_stages(ks) * 2 * ks * SLICE_BYTES + WS_BAR_BYTES + WS_SCALE_BYTES + WS_SLOT_BYTES + 32;
 }
 
+// Raw-ring variant (float-float passes up to 4 digit slices): the raw float-float operand of a
+// 32-wide chunk (128 fibers x 32 K x 8 B = 32 KB) arrives in shared memory by bulk copies that
+// the scheduler warp issues up to WS_NRAW chunks ahead, so that ~96 KB per SM are in flight
+// without holding registers; the producers cut from shared memory into two operand stages.
+// With loads issued by the producers themselves, one prefetched chunk (32 KB per SM, the
+// register budget) at ~1.5 us of loaded latency capped the input near half the HBM bandwidth.
+constexpr int WS_NRAW = 3;
+constexpr int WS_RAW_BYTES = 128 * KC * 8;
+constexpr int WS_RR_STAGES = 2;
+static_assert(3 * WS_RR_STAGES + 3 + 2 * WS_SLOTS + 2 * WS_NRAW <= WS_BAR_BYTES / 8, "mbarrier area (raw ring)");
+
+size_t ws_smem_bytes_rr(int ks) {
+  return (size_t)WS_RR_STAGES * 2 * ks * SLICE_BYTES + (size_t)WS_NRAW * WS_RAW_BYTES + WS_BAR_BYTES + WS_SCALE_BYTES +
+         WS_SLOT_BYTES + 32;
+}
+
 
 // read slot tc % WS_SLOTS once it is filled, then release it
 __device__ __forceinline__ bool ws_get(const WsSlot* slots, uint64_t* slot_full, uint64_t* slot_empty, uint32_t tc,
@@ -551,15 +570,94 @@ __device__ __forceinline__ void ws_load_rows(const WsSlot& S, int w, int lane, i
   }
 }
 
-template <int KS, bool IN_F64, bool TRANS>
+// the slot of a tile of the warp-specialised kernel; job moves forward only (the tiles of a
+// CTA increase)
+template <int KS, bool TRANS>
+__device__ __forceinline__ void ws_make_slot(const GPass& P, long long tile, int& job, WsSlot& S) {
+  int lo = job, hi = P.njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.jobs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  job = lo;
+  const GJob& J = P.jobs[job];
+  const long long tj = tile - J.tile_begin;
+  const long long rtiles = TRANS ? (J.R + 127) / 128 : 1;
+  const long long per_rb = TRANS ? J.B0 * rtiles : (J.B0 + 127) / 128;
+  const int rb = (int)(tj / per_rb);
+  const long long th = tj % per_rb;
+  S.in = job_in(P, J);
+  S.out = job_out(P, J);
+  const int nsub = (J.n + 31) / 32;
+  S.ebase = J.eslices + (size_t)rb * (size_t)nsub * KS * SLICE_BYTES;
+  S.rexp = J.rexp + 128 * rb;
+  S.out_exp = J.out_exp;
+  S.R = J.R;
+  S.B0 = J.B0;
+  S.base = TRANS ? (th / rtiles) * (long long)J.n * J.R : 0;
+  S.g0 = TRANS ? (th % rtiles) * 128 : th * 128;
+  S.n = J.n;
+  S.nsub = nsub;
+  S.rb = rb;
+  S.eX = job_in_exp(J);
+  S.nrows_e = min(128, J.n - 128 * rb);
+  S.out_f64 = J.out_f64;
+}
+
+// TMA tensor copies (tile mode, no swizzle) of a box of the tensor map's global tensor into
+// shared memory; elements outside the tensor arrive as zeros and count toward the bytes
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int x, int y, int z, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
+// Raw-ring variant: chunk c of a tile into raw buffer rbuf by one TMA copy (issued by one
+// thread).  Fastest-axis passes: the job's input as a 2D tensor {n, B0} of 8-byte elements,
+// box {32, 128} at (32 c, g0) -> 128 rows of 256 B.  Transposed passes: 3D {R, n, B0}, box
+// {128, 32, 1} at (g0, 32 c, b0) -> 32 K rows of 1 KB.  The innermost coordinate (32 c resp.
+// g0, a multiple of 128) times 8 bytes is a multiple of 16; fibers past R or B0 and K past n
+// arrive as zeros.  The barrier expects the full 32 KB box.
+template <bool TRANS>
+__device__ __forceinline__ void ws_raw_tma(const GPass& P, int job, const WsSlot& S, int c, uint8_t* rbuf,
+                                           uint64_t* full) {
+  mbar_expect_tx(smem_u32(full), (uint32_t)WS_RAW_BYTES);
+#ifdef PHIKRON_CHECKED
+  const size_t in_bytes = 8ull * (size_t)S.n * (size_t)S.B0 * (size_t)(TRANS ? S.R : 1);
+  if (!PK_CK(S.in, in_bytes, chk::SITE_MODE_LOAD)) {   // the zero block instead of the box
+    bulk_copy_g2s(smem_u32(rbuf), chk::g_state->zero, (uint32_t)WS_RAW_BYTES, smem_u32(full));
+    return;
+  }
+#endif
+  const void* tm = static_cast<const uint8_t*>(P.tmaps) + 128 * (size_t)job;
+  if (!TRANS)
+    tma_load_2d(smem_u32(rbuf), tm, KC * c, (int)S.g0, smem_u32(full));
+  else
+    tma_load_3d(smem_u32(rbuf), tm, (int)S.g0, KC * c, (int)(S.base / ((long long)S.n * S.R)), smem_u32(full));
+}
+
+template <int KS, bool IN_F64, bool TRANS, bool RR = false>
 __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
+  static_assert(!RR || (!IN_F64 && KS <= 4), "raw ring: float-float passes up to 4 digit slices");
   PK_CHECK_TABLES(P);
   const unsigned long long wl = P.wait_ns;  // limit of every bounded wait
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int HALF_BYTES = KS * SLICE_BYTES;
   constexpr int STAGE_BYTES = 2 * HALF_BYTES;
-  constexpr int NST = ws_stages(KS);
-  uint8_t* tail = smem + NST * STAGE_BYTES;
+  constexpr int NST = RR ? WS_RR_STAGES : ws_stages(KS);
+  constexpr int NRAW = RR ? WS_NRAW : 0;
+  uint8_t* rawring = smem + NST * STAGE_BYTES;   // [NRAW] raw chunks (raw-ring variant)
+  uint8_t* tail = rawring + NRAW * WS_RAW_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
   uint64_t* full_x = bars;              // [NST]
   uint64_t* full_e = bars + NST;        // [NST]
@@ -569,6 +667,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
   uint64_t* done = bars + 3 * NST + 2;
   uint64_t* slot_full = bars + 3 * NST + 3;            // [WS_SLOTS]
   uint64_t* slot_empty = bars + 3 * NST + 3 + WS_SLOTS;  // [WS_SLOTS]
+  uint64_t* raw_full = bars + 3 * NST + 3 + 2 * WS_SLOTS;   // [NRAW] raw chunk landed
+  uint64_t* raw_empty = raw_full + NRAW;                   // [NRAW] producers read it
   float* scale_s = reinterpret_cast<float*>(tail + WS_BAR_BYTES);  // 128 floats
   WsSlot* slots = reinterpret_cast<WsSlot*>(tail + WS_BAR_BYTES + WS_SCALE_BYTES);
   uint32_t* tmem_s = reinterpret_cast<uint32_t*>(tail + WS_BAR_BYTES + WS_SCALE_BYTES + WS_SLOT_BYTES);
@@ -589,6 +689,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_full[q])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&slot_empty[q])), "r"(WS_SLOT_READERS));
     }
+    for (int q = 0; q < NRAW; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&raw_full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&raw_empty[q])), "r"(WS_PROD));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_s = 0;
   }
@@ -602,7 +706,94 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_s;
 
-  if (warp < WS_EPI0) {
+  if (RR && warp < WS_EPI0) {
+    // ------------------------------------------------------------ producers (raw ring)
+    const int orow = tid & 127;
+    const int kh = tid >> 7;
+    const int q = lane & 15;
+    uint32_t it = 0, tc = 0;
+    int e_last = -1;          // thread 0: chunk of the latest E bulk copy
+    bool stop = false;
+    for (long long tile = blockIdx.x; tile < total_tiles && !stop; tile += gridDim.x, ++tc) {
+      WsSlot S;
+      if (!ws_get(slots, slot_full, slot_empty, tc, S, wl)) ws_fail(abort_s, status);
+      if (*abort_s) break;
+      const float xsc = pow2f_full(-S.eX);
+      const int nr = (int)min(128LL, TRANS ? S.R - S.g0 : S.B0 - S.g0);   // valid fibers of the tile
+      for (int c = 0; c < S.nsub; ++c, ++it) {
+        const uint32_t st = it % NST, use = it / NST;
+        const uint32_t r = it % NRAW, ru = it / NRAW;
+        uint8_t* sX = smem + st * STAGE_BYTES;
+        uint8_t* sE = sX + HALF_BYTES;
+        const uint8_t* rb = rawring + r * WS_RAW_BYTES;
+        const int kv = min(KC, S.n - KC * c);
+        if (use >= 1 && !mbar_wait(smem_u32(&empty[st]), (use - 1) & 1u, wl)) ws_fail(abort_s, status);
+        if (!mbar_wait(smem_u32(&raw_full[r]), ru & 1u, wl)) ws_fail(abort_s, status);
+        if (*abort_s) { stop = true; break; }
+        if (tid == 0) {
+          e_last = (int)it;
+          mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)HALF_BYTES);
+          bulk_copy_g2s(smem_u32(sE), PK_CK_SRC(S.ebase + (size_t)c * HALF_BYTES, HALF_BYTES, chk::SITE_MODE_ECOPY),
+                        (uint32_t)HALF_BYTES, smem_u32(&full_e[st]));
+        }
+        if constexpr (!TRANS) {
+          // piece j: values k = 2q, 2q + 1 of row 16 w + 2 j + lane / 16 (16 lanes read a row's
+          // 256 contiguous bytes) -> 4 bytes of every slice
+          float4 v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int row = 16 * warp + 2 * j + (lane >> 4);
+            v[j] = (row < nr && 2 * q < kv) ? *reinterpret_cast<const float4*>(rb + row * 256 + q * 16)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          mbar_arrive(smem_u32(&raw_empty[r]));   // this thread's raw values are in registers
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float2 a[KS];
+            cut_ff_float2<KS>(make_float2(v[j].x, v[j].z), make_float2(v[j].y, v[j].w), xsc, a);
+            const int row = 16 * warp + 2 * j + (lane >> 4);
+            const uint32_t off = chunk_offset(row, q >> 2) + (uint32_t)(q & 3) * 4u;
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl)
+              *reinterpret_cast<uint32_t*>(sX + sl * SLICE_BYTES + off) = pack_bf16x2(a[sl].x, a[sl].y);
+          }
+        } else {
+          // fiber orow, values k = 16 kh .. 16 kh + 15 (lanes read consecutive fibers)
+          float2 f[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int k = 16 * kh + e;
+            f[e] = (orow < nr && k < kv) ? *reinterpret_cast<const float2*>(rb + k * 1024 + orow * 8)
+                                         : make_float2(0.f, 0.f);
+          }
+          mbar_arrive(smem_u32(&raw_empty[r]));
+#pragma unroll
+          for (int g2 = 0; g2 < 2; ++g2) {
+            uint32_t pk[KS][4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+              float2 a[KS];
+              cut_ff_float2<KS>(make_float2(f[8 * g2 + e].x, f[8 * g2 + e + 1].x),
+                                make_float2(f[8 * g2 + e].y, f[8 * g2 + e + 1].y), xsc, a);
+#pragma unroll
+              for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(a[sl].x, a[sl].y);
+            }
+            const uint32_t off = chunk_offset(orow, 2 * kh + g2);
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl)
+              *reinterpret_cast<uint4*>(sX + sl * SLICE_BYTES + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&full_x[st]));
+      }
+    }
+    if (tid == 0 && *abort_s) {
+      // bulk copies still in flight must land before the CTA's shared memory is released
+      for (int k = e_last; k >= 0 && k >= e_last - (NST - 1); --k)
+        mbar_wait(smem_u32(&full_e[k % NST]), ((uint32_t)k / NST) & 1u, CLEANUP_WAIT_NS);
+    }
+  } else if (!RR && warp < WS_EPI0) {
     // ------------------------------------------------------------ producers
     const int orow = tid & 127;
     const int kh = tid >> 7;  // k-groups 2*kh, 2*kh + 1 of every 32-wide chunk
@@ -895,7 +1086,38 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       mma_commit(smem_u32(done));
       if (issued) mbar_wait(smem_u32(done), 0u, CLEANUP_WAIT_NS);
     }
-  } else if (warp == WS_SCHED && lane == 0) {
+  } else if (RR && warp == WS_SCHED) {
+    // ------------------------------------------------------------ scheduler + raw copies (warp 13)
+    int job = 0;
+    uint32_t tc = 0, it = 0;
+    long long r_last = -1;   // chunk of the latest raw copy
+    bool stop = false;
+    for (long long tile = blockIdx.x; tile < total_tiles && !stop; tile += gridDim.x, ++tc) {
+      const uint32_t q = tc % WS_SLOTS;
+      bool ok = tc < WS_SLOTS || mbar_wait(smem_u32(&slot_empty[q]), ((tc / WS_SLOTS) - 1) & 1u, wl);
+      if (!ok) ws_fail(abort_s, status);
+      if (__any_sync(0xffffffffu, !ok || *abort_s)) break;   // warp-uniform
+      WsSlot L;
+      ws_make_slot<KS, TRANS>(P, tile, job, L);   // every lane computes the same slot
+      if (lane == 0) {
+        slots[q] = L;
+        mbar_arrive(smem_u32(&slot_full[q]));
+      }
+      for (int c = 0; c < L.nsub; ++c, ++it) {
+        const uint32_t r = it % NRAW, ru = it / NRAW;
+        ok = ru == 0 || mbar_wait(smem_u32(&raw_empty[r]), (ru - 1) & 1u, wl);
+        if (!ok) ws_fail(abort_s, status);
+        if (__any_sync(0xffffffffu, !ok || *abort_s)) { stop = true; break; }
+        if (lane == 0) ws_raw_tma<TRANS>(P, job, L, c, rawring + r * WS_RAW_BYTES, &raw_full[r]);
+        r_last = it;
+      }
+    }
+    if (lane == 0 && *abort_s) {
+      // raw copies still in flight must land before the CTA's shared memory is released
+      for (long long k = r_last; k >= 0 && k >= r_last - (NRAW - 1); --k)
+        mbar_wait(smem_u32(&raw_full[k % NRAW]), (uint32_t)(k / NRAW) & 1u, CLEANUP_WAIT_NS);
+    }
+  } else if (!RR && warp == WS_SCHED && lane == 0) {
     // ------------------------------------------------------------ scheduler (warp 13, lane 0)
     int job = 0;
     uint32_t tc = 0;
@@ -904,36 +1126,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       if (tc >= WS_SLOTS && !mbar_wait(smem_u32(&slot_empty[q]), ((tc / WS_SLOTS) - 1) & 1u, wl))
         ws_fail(abort_s, status);
       if (*abort_s) break;
-      // tiles of this CTA increase, so the job index only moves forward
-      int lo = job, hi = P.njobs - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (P.jobs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
-      }
-      job = lo;
-      const GJob& J = P.jobs[job];
-      const long long tj = tile - J.tile_begin;
-      const long long rtiles = TRANS ? (J.R + 127) / 128 : 1;
-      const long long per_rb = TRANS ? J.B0 * rtiles : (J.B0 + 127) / 128;
-      const int rb = (int)(tj / per_rb);
-      const long long th = tj % per_rb;
-      WsSlot& S = slots[q];
-      S.in = job_in(P, J);
-      S.out = job_out(P, J);
-      const int nsub = (J.n + 31) / 32;
-      S.ebase = J.eslices + (size_t)rb * (size_t)nsub * KS * SLICE_BYTES;
-      S.rexp = J.rexp + 128 * rb;
-      S.out_exp = J.out_exp;
-      S.R = J.R;
-      S.B0 = J.B0;
-      S.base = TRANS ? (th / rtiles) * (long long)J.n * J.R : 0;
-      S.g0 = TRANS ? (th % rtiles) * 128 : th * 128;
-      S.n = J.n;
-      S.nsub = nsub;
-      S.rb = rb;
-      S.eX = job_in_exp(J);
-      S.nrows_e = min(128, J.n - 128 * rb);
-      S.out_f64 = J.out_f64;
+      ws_make_slot<KS, TRANS>(P, tile, job, slots[q]);
       mbar_arrive(smem_u32(&slot_full[q]));
     }
   }
@@ -1336,12 +1529,18 @@ size_t smem_bytes(int ks, int sub) {
 }
 
 template <int KS, int SUB, bool IN_F64, bool TRANS>
-int launch_one(const GPass& P, int grid, bool ws, int* status, cudaStream_t st) {
+int launch_one(const GPass& P, int grid, bool ws, bool rr, int* status, cudaStream_t st) {
   // the warp-specialised kernel is built for 32-wide K chunks only (its 15 warps leave ~128
   // registers a thread, too few for the doubled raw-value buffers of 64-wide chunks)
   const bool use_ws = ws && SUB == 1;
-  const size_t sm = use_ws ? ws_smem_bytes(KS) : smem_bytes(KS, SUB);
+  size_t sm = use_ws ? ws_smem_bytes(KS) : smem_bytes(KS, SUB);
   auto kern = use_ws ? mode_kernel_ws<KS, IN_F64, TRANS> : mode_kernel<KS, SUB, IN_F64, TRANS>;
+  if constexpr (!IN_F64 && KS <= 4 && SUB == 1) {
+    if (use_ws && rr) {
+      kern = mode_kernel_ws<KS, false, TRANS, true>;
+      sm = ws_smem_bytes_rr(KS);
+    }
+  }
   const int threads = use_ws ? WS_THREADS : NTHREADS;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) {
@@ -1356,12 +1555,12 @@ int launch_one(const GPass& P, int grid, bool ws, int* status, cudaStream_t st) 
 }
 
 template <int KS, int SUB>
-int launch_ks(const GPass& P, bool in_f64, bool trans, int grid, bool ws, int* status, cudaStream_t st) {
+int launch_ks(const GPass& P, bool in_f64, bool trans, int grid, bool ws, bool rr, int* status, cudaStream_t st) {
   if (in_f64)
-    return trans ? launch_one<KS, SUB, true, true>(P, grid, ws, status, st)
-                 : launch_one<KS, SUB, true, false>(P, grid, ws, status, st);
-  return trans ? launch_one<KS, SUB, false, true>(P, grid, ws, status, st)
-               : launch_one<KS, SUB, false, false>(P, grid, ws, status, st);
+    return trans ? launch_one<KS, SUB, true, true>(P, grid, ws, false, status, st)
+                 : launch_one<KS, SUB, true, false>(P, grid, ws, false, status, st);
+  return trans ? launch_one<KS, SUB, false, true>(P, grid, ws, rr, status, st)
+               : launch_one<KS, SUB, false, false>(P, grid, ws, rr, status, st);
 }
 
 template <int KS, bool IN_F64, bool TRANS>
@@ -1390,6 +1589,7 @@ int launch_db_ks(const GPass& P, bool in_f64, bool trans, int grid, int* status,
 int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) {
   if (P.njobs <= 0 || P.total_tiles <= 0) return PHIKRON_OK;
   const int grid = (int)std::min<long long>(P.total_tiles, S.grid);
+  const bool rr = S.rr && P.tmaps != nullptr;   // the raw ring needs its tensor maps
   if (S.db) {
     switch (S.slices) {
       case 3: return launch_db_ks<3>(P, S.in_f64, S.trans, grid, status, st);
@@ -1403,17 +1603,64 @@ int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) 
   }
   if (S.sub == 1) {
     switch (S.slices) {
-      case 3: return launch_ks<3, 1>(P, S.in_f64, S.trans, grid, S.ws, status, st);
-      case 4: return launch_ks<4, 1>(P, S.in_f64, S.trans, grid, S.ws, status, st);
-      case 5: return launch_ks<5, 1>(P, S.in_f64, S.trans, grid, S.ws, status, st);
-      case 6: return launch_ks<6, 1>(P, S.in_f64, S.trans, grid, S.ws, status, st);
+      case 3: return launch_ks<3, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, status, st);
+      case 4: return launch_ks<4, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, status, st);
+      case 5: return launch_ks<5, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, status, st);
+      case 6: return launch_ks<6, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, status, st);
       default: break;
     }
   } else if (S.sub == 2 && S.slices == 3) {
-    return launch_ks<3, 2>(P, S.in_f64, S.trans, grid, S.ws, status, st);
+    return launch_ks<3, 2>(P, S.in_f64, S.trans, grid, S.ws, false, status, st);
   }
   set_error("tc mode pass: unsupported (slices, sub-chunks) combination");
   return PHIKRON_EINVAL;
+}
+
+// TMA tensor maps of the inputs of a raw-ring pass's jobs (one 128-byte CUtensorMap each, in
+// job order), encoded with the driver's cuTensorMapEncodeTiled (looked up through the runtime,
+// no link against the driver library).  PHIKRON_ENOTSUP if the driver lacks it or refuses a map.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encode_raw_maps(const GJob* jobs, int njobs, bool trans, uint8_t* out) {
+  static EncodeTiled encode = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<EncodeTiled>(fn);
+    cudaGetLastError();
+  }
+  if (!encode) return PHIKRON_ENOTSUP;
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  for (int j = 0; j < njobs; ++j) {
+    const GJob& J = jobs[j];
+    CUtensorMap m;
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r;
+    if (!trans) {
+      const cuuint64_t dim[2] = {(cuuint64_t)J.n, (cuuint64_t)J.B0};
+      const cuuint64_t str[1] = {(cuuint64_t)J.n * 8};
+      const cuuint32_t box[2] = {(cuuint32_t)KC, 128};
+      r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(J.in), dim, str, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+      const cuuint64_t dim[3] = {(cuuint64_t)J.R, (cuuint64_t)J.n, (cuuint64_t)J.B0};
+      const cuuint64_t str[2] = {(cuuint64_t)J.R * 8, (cuuint64_t)J.n * J.R * 8};
+      const cuuint32_t box[3] = {128, (cuuint32_t)KC, 1};
+      r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(J.in), dim, str, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) return PHIKRON_ENOTSUP;
+    std::memcpy(out + 128 * (size_t)j, &m, 128);
+  }
+  return PHIKRON_OK;
 }
 
 int set_ptrtab(void** tab, const PtrArgs& args, cudaStream_t st) {
