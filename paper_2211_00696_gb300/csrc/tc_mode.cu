@@ -646,6 +646,118 @@ __device__ __forceinline__ void ws_raw_tma(const GPass& P, int job, const WsSlot
     tma_load_3d(smem_u32(rbuf), tm, (int)S.g0, KC * c, (int)(S.base / ((long long)S.n * S.R)), smem_u32(full));
 }
 
+// The epilogue's work on TMEM columns [c0, c1) (multiples of 16) of lane et (lane_base = its
+// lane quarter): the four level accumulators combined into float-float, scaled by the row
+// exponents, stored (float-float or float64); returns the largest |hi| stored.  Run by whole
+// warps (tcgen05.ld is warp-collective).
+template <int KS, bool TRANS>
+__device__ __forceinline__ float ws_epi_cols(const WsSlot& S, uint32_t lane_base, int et, int c0, int c1,
+                                             const float* scale_s) {
+  float mxf = 0.0f;  // largest |hi| stored (one FMNMX per element)
+  if (TRANS) {
+    // TMEM lane = fiber r, column = output row i of this row block; stores coalesce over lanes
+    const long long g = S.g0 + et;
+    const bool vg = g < S.R;
+    const long long o0 = S.base + (long long)(128 * S.rb) * S.R + g;
+    for (int cc = c0; cc < min(c1, S.nrows_e); cc += 16) {
+      float d2[16], d3[16], d4[16], d5[16];
+      tmem_ld16(lane_base + (uint32_t)cc, d2);
+      tmem_ld16(lane_base + 128u + (uint32_t)cc, d3);
+      tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
+      if (KS >= 4) tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
+      tmem_wait_ld();
+      // the float64 / float-float choice is made per group, so that the 16 columns of the
+      // unrolled body stay straight-line code the compiler can interleave
+      if (vg && !S.out_f64) {
+        float2* dst = reinterpret_cast<float2*>(S.out) + o0 + (long long)cc * S.R;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float2 hi, lo;
+          ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
+                          make_float2(d4[j], d4[j + 1]),
+                          KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
+          const float2 sc = *reinterpret_cast<const float2*>(scale_s + cc + j);
+          hi = mul2(hi, sc);
+          lo = mul2(lo, sc);
+          st_ck(dst + (long long)j * S.R, make_float2(hi.x, lo.x), chk::SITE_MODE_STORE);
+          st_ck(dst + (long long)(j + 1) * S.R, make_float2(hi.y, lo.y), chk::SITE_MODE_STORE);
+          mxf = fmaxf(mxf, fmaxf(fabsf(hi.x), fabsf(hi.y)));
+        }
+      } else if (vg) {
+        double* dst = reinterpret_cast<double*>(S.out) + o0 + (long long)cc * S.R;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float2 hi, lo;
+          ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
+                          make_float2(d4[j], d4[j + 1]),
+                          KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
+          const float2 sc = *reinterpret_cast<const float2*>(scale_s + cc + j);
+          hi = mul2(hi, sc);
+          lo = mul2(lo, sc);
+          st_ck(dst + (long long)j * S.R, ff_to_f64(hi.x, lo.x), chk::SITE_MODE_STORE);
+          st_ck(dst + (long long)(j + 1) * S.R, ff_to_f64(hi.y, lo.y), chk::SITE_MODE_STORE);
+          mxf = fmaxf(mxf, fmaxf(fabsf(hi.x), fabsf(hi.y)));
+        }
+      }
+    }
+  } else {
+    // TMEM lane = output row i of this row block, column = fiber; stores coalesce over lanes
+    const bool vi = et < S.nrows_e;
+    const int ncols = (int)min(128LL, S.B0 - S.g0);
+    const float sc = scale_s[et];
+    const long long o0 = S.g0 * (long long)S.n + 128 * S.rb + et;
+    for (int cc = c0; cc < min(c1, ncols); cc += 16) {
+      float d2[16], d3[16], d4[16], d5[16];
+      tmem_ld16(lane_base + (uint32_t)cc, d2);
+      tmem_ld16(lane_base + 128u + (uint32_t)cc, d3);
+      tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
+      if (KS >= 4) tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
+      tmem_wait_ld();
+      const int jn = min(16, ncols - cc);  // columns of this group inside the tile
+      if (vi && !S.out_f64) {
+        float2* dst = reinterpret_cast<float2*>(S.out) + o0 + (long long)cc * S.n;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float2 hi, lo;
+          ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
+                          make_float2(d4[j], d4[j + 1]),
+                          KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
+          hi = mul2(hi, make_float2(sc, sc));
+          lo = mul2(lo, make_float2(sc, sc));
+          if (j < jn) {
+            st_ck(dst + (long long)j * S.n, make_float2(hi.x, lo.x), chk::SITE_MODE_STORE);
+            mxf = fmaxf(mxf, fabsf(hi.x));
+          }
+          if (j + 1 < jn) {
+            st_ck(dst + (long long)(j + 1) * S.n, make_float2(hi.y, lo.y), chk::SITE_MODE_STORE);
+            mxf = fmaxf(mxf, fabsf(hi.y));
+          }
+        }
+      } else if (vi) {
+        double* dst = reinterpret_cast<double*>(S.out) + o0 + (long long)cc * S.n;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float2 hi, lo;
+          ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
+                          make_float2(d4[j], d4[j + 1]),
+                          KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
+          hi = mul2(hi, make_float2(sc, sc));
+          lo = mul2(lo, make_float2(sc, sc));
+          if (j < jn) {
+            st_ck(dst + (long long)j * S.n, ff_to_f64(hi.x, lo.x), chk::SITE_MODE_STORE);
+            mxf = fmaxf(mxf, fabsf(hi.x));
+          }
+          if (j + 1 < jn) {
+            st_ck(dst + (long long)(j + 1) * S.n, ff_to_f64(hi.y, lo.y), chk::SITE_MODE_STORE);
+            mxf = fmaxf(mxf, fabsf(hi.y));
+          }
+        }
+      }
+    }
+  }
+  return mxf;
+}
+
 template <int KS, bool IN_F64, bool TRANS, bool RR = false>
 __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
   static_assert(!RR || (!IN_F64 && KS <= 4), "raw ring: float-float passes up to 4 digit slices");
@@ -930,108 +1042,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       // the vote is also the barrier after the scale writes; every epilogue thread decides alike
       if (epi_vote_any(!ok || *abort_s)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float mxf = 0.0f;  // largest |hi| stored (one FMNMX per element)
-      if (TRANS) {
-        // TMEM lane = fiber r, column = output row i of this row block; stores coalesce over lanes
-        const long long g = S.g0 + et;
-        const bool vg = g < S.R;
-        const long long o0 = S.base + (long long)(128 * S.rb) * S.R + g;
-        for (int cc = 0; cc < S.nrows_e; cc += 16) {
-          float d2[16], d3[16], d4[16], d5[16];
-          tmem_ld16(lane_base + (uint32_t)cc, d2);
-          tmem_ld16(lane_base + 128u + (uint32_t)cc, d3);
-          tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
-          if (KS >= 4) tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
-          tmem_wait_ld();
-          // the float64 / float-float choice is made per group, so that the 16 columns of the
-          // unrolled body stay straight-line code the compiler can interleave
-          if (vg && !S.out_f64) {
-            float2* dst = reinterpret_cast<float2*>(S.out) + o0 + (long long)cc * S.R;
-#pragma unroll
-            for (int j = 0; j < 16; j += 2) {
-              float2 hi, lo;
-              ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
-                              make_float2(d4[j], d4[j + 1]),
-                              KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
-              const float2 sc = *reinterpret_cast<const float2*>(scale_s + cc + j);
-              hi = mul2(hi, sc);
-              lo = mul2(lo, sc);
-              st_ck(dst + (long long)j * S.R, make_float2(hi.x, lo.x), chk::SITE_MODE_STORE);
-              st_ck(dst + (long long)(j + 1) * S.R, make_float2(hi.y, lo.y), chk::SITE_MODE_STORE);
-              mxf = fmaxf(mxf, fmaxf(fabsf(hi.x), fabsf(hi.y)));
-            }
-          } else if (vg) {
-            double* dst = reinterpret_cast<double*>(S.out) + o0 + (long long)cc * S.R;
-#pragma unroll
-            for (int j = 0; j < 16; j += 2) {
-              float2 hi, lo;
-              ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
-                              make_float2(d4[j], d4[j + 1]),
-                              KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
-              const float2 sc = *reinterpret_cast<const float2*>(scale_s + cc + j);
-              hi = mul2(hi, sc);
-              lo = mul2(lo, sc);
-              st_ck(dst + (long long)j * S.R, ff_to_f64(hi.x, lo.x), chk::SITE_MODE_STORE);
-              st_ck(dst + (long long)(j + 1) * S.R, ff_to_f64(hi.y, lo.y), chk::SITE_MODE_STORE);
-              mxf = fmaxf(mxf, fmaxf(fabsf(hi.x), fabsf(hi.y)));
-            }
-          }
-        }
-      } else {
-        // TMEM lane = output row i of this row block, column = fiber; stores coalesce over lanes
-        const bool vi = et < S.nrows_e;
-        const int ncols = (int)min(128LL, S.B0 - S.g0);
-        const float sc = scale_s[et];
-        const long long o0 = S.g0 * (long long)S.n + 128 * S.rb + et;
-        for (int cc = 0; cc < ncols; cc += 16) {
-          float d2[16], d3[16], d4[16], d5[16];
-          tmem_ld16(lane_base + (uint32_t)cc, d2);
-          tmem_ld16(lane_base + 128u + (uint32_t)cc, d3);
-          tmem_ld16(lane_base + 256u + (uint32_t)cc, d4);
-          if (KS >= 4) tmem_ld16(lane_base + 384u + (uint32_t)cc, d5);
-          tmem_wait_ld();
-          const int jn = min(16, ncols - cc);  // columns of this group inside the tile
-          if (vi && !S.out_f64) {
-            float2* dst = reinterpret_cast<float2*>(S.out) + o0 + (long long)cc * S.n;
-#pragma unroll
-            for (int j = 0; j < 16; j += 2) {
-              float2 hi, lo;
-              ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
-                              make_float2(d4[j], d4[j + 1]),
-                              KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
-              hi = mul2(hi, make_float2(sc, sc));
-              lo = mul2(lo, make_float2(sc, sc));
-              if (j < jn) {
-                st_ck(dst + (long long)j * S.n, make_float2(hi.x, lo.x), chk::SITE_MODE_STORE);
-                mxf = fmaxf(mxf, fabsf(hi.x));
-              }
-              if (j + 1 < jn) {
-                st_ck(dst + (long long)(j + 1) * S.n, make_float2(hi.y, lo.y), chk::SITE_MODE_STORE);
-                mxf = fmaxf(mxf, fabsf(hi.y));
-              }
-            }
-          } else if (vi) {
-            double* dst = reinterpret_cast<double*>(S.out) + o0 + (long long)cc * S.n;
-#pragma unroll
-            for (int j = 0; j < 16; j += 2) {
-              float2 hi, lo;
-              ff_combine2<KS>(make_float2(d2[j], d2[j + 1]), make_float2(d3[j], d3[j + 1]),
-                              make_float2(d4[j], d4[j + 1]),
-                              KS >= 4 ? make_float2(d5[j], d5[j + 1]) : make_float2(0.0f, 0.0f), hi, lo);
-              hi = mul2(hi, make_float2(sc, sc));
-              lo = mul2(lo, make_float2(sc, sc));
-              if (j < jn) {
-                st_ck(dst + (long long)j * S.n, ff_to_f64(hi.x, lo.x), chk::SITE_MODE_STORE);
-                mxf = fmaxf(mxf, fabsf(hi.x));
-              }
-              if (j + 1 < jn) {
-                st_ck(dst + (long long)(j + 1) * S.n, ff_to_f64(hi.y, lo.y), chk::SITE_MODE_STORE);
-                mxf = fmaxf(mxf, fabsf(hi.y));
-              }
-            }
-          }
-        }
-      }
+      const float mxf = ws_epi_cols<KS, TRANS>(S, lane_base, et, 0, 128, scale_s);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(tmem_empty));
       uint32_t mx = __float_as_uint(mxf);  // non-negative: bit patterns order like the values
