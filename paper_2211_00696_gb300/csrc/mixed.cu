@@ -931,7 +931,7 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       for (const GJob& j : jobs)
         direct16 = direct16 && j.in_tab < 0 && (reinterpret_cast<uintptr_t>(j.in) & 15u) == 0 && j.n % 16 == 0 &&
                    (!trans || j.R % 16 == 0);
-      sh.rr = cfg.rr && cfg.ws && !sh.in_f64 && cfg.slices <= 4 && direct16;
+      sh.rr = cfg.rr && (cfg.ws || sh.db) && !sh.in_f64 && cfg.slices <= 4 && direct16;
       if (dims == 1) sh.trans = false;
       // all jobs of one pass share the formulation (same axis d)
       B.mode_step(jobs, sh);
@@ -939,7 +939,8 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
         Step& stp = B.steps.back();
         const size_t off = B.tmaps.size();
         B.tmaps.resize(off + 128 * (size_t)stp.count);
-        if (tc::encode_raw_maps(B.gjobs.data() + stp.off, stp.count, sh.trans, B.tmaps.data() + off) == PHIKRON_OK) {
+        if (tc::encode_raw_maps(B.gjobs.data() + stp.off, stp.count, sh.trans, sh.db ? 64 : 128, B.tmaps.data() + off) ==
+            PHIKRON_OK) {
           stp.tmap_off = (long long)(off / 128);
         } else {   // no tensor maps: the register-loading kernel
           B.tmaps.resize(off);

@@ -64,7 +64,8 @@ namespace tc {
 int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st);
 int set_ptrtab(void** tab, const PtrArgs& args, cudaStream_t st);
 // TMA tensor maps (128 bytes each, job order) of the inputs of a raw-ring mode pass's jobs
-int encode_raw_maps(const GJob* jobs, int njobs, bool trans, uint8_t* out);
+// (boxes of `fibers` = 128 fibers for the warp-specialised kernel, 64 for the double-buffered one)
+int encode_raw_maps(const GJob* jobs, int njobs, bool trans, int fibers, uint8_t* out);
 size_t smem_bytes(int ks, int sub);
 }  // namespace tc
 

@@ -1168,6 +1168,36 @@ size_t db_smem_bytes(int ks) {
   return (size_t)db_stages(ks) * ks * (DB_XSLICE + SLICE_BYTES) + DB_STAGE_BYTES + WS_BAR_BYTES + WS_SLOT_BYTES + 32;
 }
 
+// Raw-ring variant of the double-buffered kernel (float-float passes up to 4 slices): raw
+// chunks of 64 fibers x 32 K (16 KB) by one TMA tensor copy each, three in flight, two stages
+constexpr int DB_RAW_BYTES = 64 * KC * 8;
+static_assert(3 * WS_RR_STAGES + 5 + 2 * WS_SLOTS + 2 * WS_NRAW <= WS_BAR_BYTES / 8, "mbarrier area (db raw ring)");
+
+size_t db_smem_bytes_rr(int ks) {
+  return (size_t)WS_RR_STAGES * ks * (DB_XSLICE + SLICE_BYTES) + DB_STAGE_BYTES + (size_t)WS_NRAW * DB_RAW_BYTES +
+         WS_BAR_BYTES + WS_SLOT_BYTES + 32;
+}
+
+// chunk c of a 64-fiber tile into raw buffer rbuf by one TMA copy (see ws_raw_tma; boxes
+// {32, 64} resp. {64, 32, 1}, tensor maps encoded for 64-fiber boxes)
+template <bool TRANS>
+__device__ __forceinline__ void db_raw_tma(const GPass& P, int job, const WsSlot& S, int c, uint8_t* rbuf,
+                                           uint64_t* full) {
+  mbar_expect_tx(smem_u32(full), (uint32_t)DB_RAW_BYTES);
+#ifdef PHIKRON_CHECKED
+  const size_t in_bytes = 8ull * (size_t)S.n * (size_t)S.B0 * (size_t)(TRANS ? S.R : 1);
+  if (!PK_CK(S.in, in_bytes, chk::SITE_MODE_LOAD)) {
+    bulk_copy_g2s(smem_u32(rbuf), chk::g_state->zero, (uint32_t)DB_RAW_BYTES, smem_u32(full));
+    return;
+  }
+#endif
+  const void* tm = static_cast<const uint8_t*>(P.tmaps) + 128 * (size_t)job;
+  if (!TRANS)
+    tma_load_2d(smem_u32(rbuf), tm, KC * c, (int)S.g0, smem_u32(full));
+  else
+    tma_load_3d(smem_u32(rbuf), tm, (int)S.g0, KC * c, (int)(S.base / ((long long)S.n * S.R)), smem_u32(full));
+}
+
 // 8 consecutive values (k = kc .. kc+7) of fiber g0 + fib
 template <bool IN_F64, bool TRANS>
 __device__ __forceinline__ void db_load(const WsSlot& S, int fib, int kc, Raw<IN_F64>& raw) {
@@ -1197,16 +1227,52 @@ __device__ __forceinline__ void db_load(const WsSlot& S, int fib, int kc, Raw<IN
   }
 }
 
-template <int KS, bool IN_F64, bool TRANS>
+// the slot of a 64-fiber tile of the double-buffered kernel (job moves forward only)
+template <int KS, bool TRANS>
+__device__ __forceinline__ void db_make_slot(const GPass& P, long long tile, int& job, WsSlot& S) {
+  int lo = job, hi = P.njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.jobs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  job = lo;
+  const GJob& J = P.jobs[job];
+  const long long tj = tile - J.tile_begin;
+  const long long rt = TRANS ? (J.R + 63) / 64 : 1;
+  const long long per_rb = TRANS ? J.B0 * rt : (J.B0 + 63) / 64;
+  const int rb = (int)(tj / per_rb);
+  const long long th = tj % per_rb;
+  S.in = job_in(P, J);
+  S.out = job_out(P, J);
+  const int nsub = (J.n + 31) / 32;
+  S.ebase = J.eslices + (size_t)rb * (size_t)nsub * KS * SLICE_BYTES;
+  S.rexp = J.rexp + 128 * rb;
+  S.out_exp = J.out_exp;
+  S.R = J.R;
+  S.B0 = J.B0;
+  S.base = TRANS ? (th / rt) * (long long)J.n * J.R : 0;
+  S.g0 = TRANS ? (th % rt) * 64 : th * 64;
+  S.n = J.n;
+  S.nsub = nsub;
+  S.rb = rb;
+  S.eX = job_in_exp(J);
+  S.nrows_e = min(128, J.n - 128 * rb);
+  S.out_f64 = J.out_f64;
+}
+
+template <int KS, bool IN_F64, bool TRANS, bool RR = false>
 __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_constant__ GPass P, int* status) {
+  static_assert(!RR || (!IN_F64 && KS <= 4), "raw ring: float-float passes up to 4 digit slices");
   PK_CHECK_TABLES(P);
   const unsigned long long wl = P.wait_ns;  // limit of every bounded wait
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int XBYTES = KS * DB_XSLICE;
   constexpr int STAGE = XBYTES + KS * SLICE_BYTES;
-  constexpr int NST = db_stages(KS);
+  constexpr int NST = RR ? WS_RR_STAGES : db_stages(KS);
+  constexpr int NRAW = RR ? WS_NRAW : 0;
   uint8_t* staging = smem + NST * STAGE;
-  uint8_t* tail = staging + DB_STAGE_BYTES;
+  uint8_t* rawring = staging + DB_STAGE_BYTES;   // [NRAW] raw chunks (raw-ring variant)
+  uint8_t* tail = rawring + NRAW * DB_RAW_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
   uint64_t* full_x = bars;                  // [NST]
   uint64_t* full_e = bars + NST;            // [NST]
@@ -1216,6 +1282,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
   uint64_t* done = bars + 3 * NST + 4;
   uint64_t* slot_full = bars + 3 * NST + 5;             // [WS_SLOTS]
   uint64_t* slot_empty = bars + 3 * NST + 5 + WS_SLOTS; // [WS_SLOTS]
+  uint64_t* raw_full = bars + 3 * NST + 5 + 2 * WS_SLOTS;  // [NRAW]
+  uint64_t* raw_empty = raw_full + NRAW;                  // [NRAW]
   WsSlot* slots = reinterpret_cast<WsSlot*>(tail + WS_BAR_BYTES);
   uint32_t* tmem_s = reinterpret_cast<uint32_t*>(tail + WS_BAR_BYTES + WS_SLOT_BYTES);
   volatile int* abort_s = reinterpret_cast<volatile int*>(tail + WS_BAR_BYTES + WS_SLOT_BYTES + 16);
@@ -1237,6 +1305,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_full[q])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&slot_empty[q])), "r"(WS_SLOT_READERS));
     }
+    for (int q = 0; q < NRAW; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&raw_full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&raw_empty[q])), "r"(WS_PROD));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_s = 0;
   }
@@ -1250,7 +1322,90 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_s;
 
-  if (warp < WS_EPI0) {
+  if (RR && warp < WS_EPI0) {
+    // ------------------------------------------------------------ producers (raw ring)
+    const int fib = tid & 63;   // fiber of the tile (transposed passes)
+    const int kg = tid >> 6;    // k-group (8 values) of every 32-wide chunk (transposed passes)
+    const int q = lane & 15;    // 16-byte piece of a row (fastest-axis passes)
+    uint32_t it = 0, tc = 0;
+    int e_last = -1;            // thread 0: chunk of the latest E bulk copy
+    bool stop = false;
+    for (long long tile = blockIdx.x; tile < total_tiles && !stop; tile += gridDim.x, ++tc) {
+      WsSlot S;
+      if (!ws_get(slots, slot_full, slot_empty, tc, S, wl)) ws_fail(abort_s, status);
+      if (*abort_s) break;
+      const float xsc = pow2f_full(-S.eX);
+      const int nr = (int)min(64LL, TRANS ? S.R - S.g0 : S.B0 - S.g0);   // valid fibers of the tile
+      for (int c = 0; c < S.nsub; ++c, ++it) {
+        const uint32_t st = it % NST, use = it / NST;
+        const uint32_t r = it % NRAW, ru = it / NRAW;
+        uint8_t* sX = smem + st * STAGE;
+        uint8_t* sE = sX + XBYTES;
+        const uint8_t* rb = rawring + r * DB_RAW_BYTES;
+        const int kv = min(KC, S.n - KC * c);
+        if (use >= 1 && !mbar_wait(smem_u32(&empty[st]), (use - 1) & 1u, wl)) ws_fail(abort_s, status);
+        if (!mbar_wait(smem_u32(&raw_full[r]), ru & 1u, wl)) ws_fail(abort_s, status);
+        if (*abort_s) { stop = true; break; }
+        if (tid == 0) {
+          e_last = (int)it;
+          mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)(KS * SLICE_BYTES));
+          bulk_copy_g2s(smem_u32(sE),
+                        PK_CK_SRC(S.ebase + (size_t)c * KS * SLICE_BYTES, KS * SLICE_BYTES, chk::SITE_MODE_ECOPY),
+                        (uint32_t)(KS * SLICE_BYTES), smem_u32(&full_e[st]));
+        }
+        if constexpr (!TRANS) {
+          // piece j: values k = 2q, 2q + 1 of row 8 w + 2 j + lane / 16 -> 4 bytes of every slice
+          float4 v[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int row = 8 * warp + 2 * j + (lane >> 4);
+            v[j] = (row < nr && 2 * q < kv) ? *reinterpret_cast<const float4*>(rb + row * 256 + q * 16)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          mbar_arrive(smem_u32(&raw_empty[r]));
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float2 a[KS];
+            cut_ff_float2<KS>(make_float2(v[j].x, v[j].z), make_float2(v[j].y, v[j].w), xsc, a);
+            const int row = 8 * warp + 2 * j + (lane >> 4);
+            const uint32_t off = chunk_offset(row, q >> 2) + (uint32_t)(q & 3) * 4u;
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl)
+              *reinterpret_cast<uint32_t*>(sX + sl * DB_XSLICE + off) = pack_bf16x2(a[sl].x, a[sl].y);
+          }
+        } else {
+          // fiber fib, values k = 8 kg .. 8 kg + 7 (lanes read consecutive fibers)
+          float2 f[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int k = 8 * kg + e;
+            f[e] = (fib < nr && k < kv) ? *reinterpret_cast<const float2*>(rb + k * 512 + fib * 8)
+                                        : make_float2(0.f, 0.f);
+          }
+          mbar_arrive(smem_u32(&raw_empty[r]));
+          uint32_t pk[KS][4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            float2 a[KS];
+            cut_ff_float2<KS>(make_float2(f[e].x, f[e + 1].x), make_float2(f[e].y, f[e + 1].y), xsc, a);
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = pack_bf16x2(a[sl].x, a[sl].y);
+          }
+          const uint32_t off = chunk_offset(fib, kg);
+#pragma unroll
+          for (int sl = 0; sl < KS; ++sl)
+            *reinterpret_cast<uint4*>(sX + sl * DB_XSLICE + off) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&full_x[st]));
+      }
+    }
+    if (tid == 0 && *abort_s) {
+      // bulk copies still in flight must land before the CTA's shared memory is released
+      for (int k = e_last; k >= 0 && k >= e_last - (NST - 1); --k)
+        mbar_wait(smem_u32(&full_e[k % NST]), ((uint32_t)k / NST) & 1u, CLEANUP_WAIT_NS);
+    }
+  } else if (!RR && warp < WS_EPI0) {
     // ------------------------------------------------------------ producers
     const int fib = tid & 63;   // fiber of the tile
     const int kg = tid >> 6;    // k-group (8 values) of every 32-wide chunk
@@ -1482,7 +1637,38 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       mma_commit(smem_u32(done));
       if (issued) mbar_wait(smem_u32(done), 0u, CLEANUP_WAIT_NS);
     }
-  } else if (warp == WS_SCHED && lane == 0) {
+  } else if (RR && warp == WS_SCHED) {
+    // ------------------------------------------------------------ scheduler + raw copies (warp 13)
+    int job = 0;
+    uint32_t tc = 0, it = 0;
+    long long r_last = -1;   // chunk of the latest raw copy
+    bool stop = false;
+    for (long long tile = blockIdx.x; tile < total_tiles && !stop; tile += gridDim.x, ++tc) {
+      const uint32_t q = tc % WS_SLOTS;
+      bool ok = tc < WS_SLOTS || mbar_wait(smem_u32(&slot_empty[q]), ((tc / WS_SLOTS) - 1) & 1u, wl);
+      if (!ok) ws_fail(abort_s, status);
+      if (__any_sync(0xffffffffu, !ok || *abort_s)) break;   // warp-uniform
+      WsSlot L;
+      db_make_slot<KS, TRANS>(P, tile, job, L);   // every lane computes the same slot
+      if (lane == 0) {
+        slots[q] = L;
+        mbar_arrive(smem_u32(&slot_full[q]));
+      }
+      for (int c = 0; c < L.nsub; ++c, ++it) {
+        const uint32_t r = it % NRAW, ru = it / NRAW;
+        ok = ru == 0 || mbar_wait(smem_u32(&raw_empty[r]), (ru - 1) & 1u, wl);
+        if (!ok) ws_fail(abort_s, status);
+        if (__any_sync(0xffffffffu, !ok || *abort_s)) { stop = true; break; }
+        if (lane == 0) db_raw_tma<TRANS>(P, job, L, c, rawring + r * DB_RAW_BYTES, &raw_full[r]);
+        r_last = it;
+      }
+    }
+    if (lane == 0 && *abort_s) {
+      // raw copies still in flight must land before the CTA's shared memory is released
+      for (long long k = r_last; k >= 0 && k >= r_last - (NRAW - 1); --k)
+        mbar_wait(smem_u32(&raw_full[k % NRAW]), (uint32_t)(k / NRAW) & 1u, CLEANUP_WAIT_NS);
+    }
+  } else if (!RR && warp == WS_SCHED && lane == 0) {
     // ------------------------------------------------------------ scheduler (64-fiber tiles)
     int job = 0;
     uint32_t tc = 0;
@@ -1491,35 +1677,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       if (tc >= WS_SLOTS && !mbar_wait(smem_u32(&slot_empty[q]), ((tc / WS_SLOTS) - 1) & 1u, wl))
         ws_fail(abort_s, status);
       if (*abort_s) break;
-      int lo = job, hi = P.njobs - 1;  // tiles of this CTA increase: the job index only moves forward
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (P.jobs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
-      }
-      job = lo;
-      const GJob& J = P.jobs[job];
-      const long long tj = tile - J.tile_begin;
-      const long long rt = TRANS ? (J.R + 63) / 64 : 1;
-      const long long per_rb = TRANS ? J.B0 * rt : (J.B0 + 63) / 64;
-      const int rb = (int)(tj / per_rb);
-      const long long th = tj % per_rb;
-      WsSlot& S = slots[q];
-      S.in = job_in(P, J);
-      S.out = job_out(P, J);
-      const int nsub = (J.n + 31) / 32;
-      S.ebase = J.eslices + (size_t)rb * (size_t)nsub * KS * SLICE_BYTES;
-      S.rexp = J.rexp + 128 * rb;
-      S.out_exp = J.out_exp;
-      S.R = J.R;
-      S.B0 = J.B0;
-      S.base = TRANS ? (th / rt) * (long long)J.n * J.R : 0;
-      S.g0 = TRANS ? (th % rt) * 64 : th * 64;
-      S.n = J.n;
-      S.nsub = nsub;
-      S.rb = rb;
-      S.eX = job_in_exp(J);
-      S.nrows_e = min(128, J.n - 128 * rb);
-      S.out_f64 = J.out_f64;
+      db_make_slot<KS, TRANS>(P, tile, job, slots[q]);
       mbar_arrive(smem_u32(&slot_full[q]));
     }
   }
@@ -1575,9 +1733,15 @@ int launch_ks(const GPass& P, bool in_f64, bool trans, int grid, bool ws, bool r
 }
 
 template <int KS, bool IN_F64, bool TRANS>
-int launch_db(const GPass& P, int grid, int* status, cudaStream_t st) {
-  const size_t sm = db_smem_bytes(KS);
+int launch_db(const GPass& P, int grid, bool rr, int* status, cudaStream_t st) {
+  size_t sm = db_smem_bytes(KS);
   auto kern = mode_kernel_db<KS, IN_F64, TRANS>;
+  if constexpr (!IN_F64 && KS <= 4) {
+    if (rr) {
+      kern = mode_kernel_db<KS, false, TRANS, true>;
+      sm = db_smem_bytes_rr(KS);
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) {
     set_error(std::string("tc mode kernel smem attribute: ") + cudaGetErrorString(e));
@@ -1591,10 +1755,12 @@ int launch_db(const GPass& P, int grid, int* status, cudaStream_t st) {
 }
 
 template <int KS>
-int launch_db_ks(const GPass& P, bool in_f64, bool trans, int grid, int* status, cudaStream_t st) {
+int launch_db_ks(const GPass& P, bool in_f64, bool trans, int grid, bool rr, int* status, cudaStream_t st) {
   if (in_f64)
-    return trans ? launch_db<KS, true, true>(P, grid, status, st) : launch_db<KS, true, false>(P, grid, status, st);
-  return trans ? launch_db<KS, false, true>(P, grid, status, st) : launch_db<KS, false, false>(P, grid, status, st);
+    return trans ? launch_db<KS, true, true>(P, grid, false, status, st)
+                 : launch_db<KS, true, false>(P, grid, false, status, st);
+  return trans ? launch_db<KS, false, true>(P, grid, rr, status, st)
+               : launch_db<KS, false, false>(P, grid, rr, status, st);
 }
 
 int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) {
@@ -1603,10 +1769,10 @@ int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) 
   const bool rr = S.rr && P.tmaps != nullptr;   // the raw ring needs its tensor maps
   if (S.db) {
     switch (S.slices) {
-      case 3: return launch_db_ks<3>(P, S.in_f64, S.trans, grid, status, st);
-      case 4: return launch_db_ks<4>(P, S.in_f64, S.trans, grid, status, st);
-      case 5: return launch_db_ks<5>(P, S.in_f64, S.trans, grid, status, st);
-      case 6: return launch_db_ks<6>(P, S.in_f64, S.trans, grid, status, st);
+      case 3: return launch_db_ks<3>(P, S.in_f64, S.trans, grid, rr, status, st);
+      case 4: return launch_db_ks<4>(P, S.in_f64, S.trans, grid, rr, status, st);
+      case 5: return launch_db_ks<5>(P, S.in_f64, S.trans, grid, rr, status, st);
+      case 6: return launch_db_ks<6>(P, S.in_f64, S.trans, grid, rr, status, st);
       default: break;
     }
     set_error("tc mode pass: unsupported slice count");
@@ -1634,7 +1800,7 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int encode_raw_maps(const GJob* jobs, int njobs, bool trans, uint8_t* out) {
+int encode_raw_maps(const GJob* jobs, int njobs, bool trans, int fibers, uint8_t* out) {
   static EncodeTiled encode = nullptr;
   static bool looked = false;
   if (!looked) {
@@ -1656,14 +1822,14 @@ int encode_raw_maps(const GJob* jobs, int njobs, bool trans, uint8_t* out) {
     if (!trans) {
       const cuuint64_t dim[2] = {(cuuint64_t)J.n, (cuuint64_t)J.B0};
       const cuuint64_t str[1] = {(cuuint64_t)J.n * 8};
-      const cuuint32_t box[2] = {(cuuint32_t)KC, 128};
+      const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)fibers};
       r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(J.in), dim, str, box, estr,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
       const cuuint64_t dim[3] = {(cuuint64_t)J.R, (cuuint64_t)J.n, (cuuint64_t)J.B0};
       const cuuint64_t str[2] = {(cuuint64_t)J.R * 8, (cuuint64_t)J.n * J.R * 8};
-      const cuuint32_t box[3] = {128, (cuuint32_t)KC, 1};
+      const cuuint32_t box[3] = {(cuuint32_t)fibers, (cuuint32_t)KC, 1};
       r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(J.in), dim, str, box, estr,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
