@@ -12,7 +12,7 @@ namespace phikron {
 
 struct Plan;
 
-enum StepKind { STEP_MODE = 0, STEP_WEIGHTED = 1, STEP_SQUARING = 2, STEP_EXPSCAN = 3, STEP_FUSED = 4 };
+enum StepKind { STEP_MODE = 0, STEP_WEIGHTED = 1, STEP_SQUARING = 2, STEP_EXPSCAN = 3, STEP_FUSED = 4, STEP_PRECUT = 5 };
 
 struct Step {
   int kind;

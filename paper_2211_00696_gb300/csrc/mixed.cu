@@ -701,6 +701,24 @@ struct Builder {
     steps.push_back(s);
   }
 
+  // pre-cut digit slices of float64 inputs: one block per (job, 128-fiber block, chunk)
+  void precut_step(std::vector<GJob> jobs, int slices) {
+    if (jobs.empty()) return;
+    long long t = 0;
+    for (GJob& j : jobs) {
+      j.tile_begin = t;
+      t += ((j.R + 127) / 128) * ((j.n + 31) / 32);
+    }
+    Step s{};
+    s.kind = STEP_PRECUT;
+    s.off = gjobs.size();
+    s.count = (int)jobs.size();
+    s.total = t;
+    s.shape.slices = slices;
+    gjobs.insert(gjobs.end(), jobs.begin(), jobs.end());
+    steps.push_back(s);
+  }
+
   // jobs[u].node0 indexes `nodes`; both are appended to the builder's tables
   void fused_step(std::vector<FJob> jobs, const std::vector<FNode>& nodes, const PassShape& shape, int p) {
     if (jobs.empty()) return;
@@ -764,6 +782,12 @@ bool fused_weights_default() {
 
 bool raw_ring_default() {
   const char* v = std::getenv("PHIKRON_RAW_RING");
+  return !(v && std::strcmp(v, "0") == 0);
+}
+
+// the float64 first pass reads its input's digit slices cut once (unless PHIKRON_PRECUT is "0")
+static bool precut_default() {
+  const char* v = std::getenv("PHIKRON_PRECUT");
   return !(v && std::strcmp(v, "0") == 0);
 }
 
@@ -919,6 +943,7 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       sh.in_f64 = (d == 0) && first_f64;
       sh.trans = trans;
       sh.ws = cfg.ws;
+      sh.pc = false;
       // the double-buffered kernel keeps two 32-wide chunks of a job in flight: n >= 64 in
       // every job of the pass; smaller factors take the warp-specialised kernel
       int minn = 1 << 30;
@@ -934,6 +959,35 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       sh.rr = cfg.rr && (cfg.ws || sh.db) && !sh.in_f64 && cfg.slices <= 4 && direct16;
       if (dims == 1) sh.trans = false;
       // all jobs of one pass share the formulation (same axis d)
+      // the float64 first pass of a chain whose vectors share their unit's input: that input's
+      // digit slices are cut once per unit (into the unit's second work buffer, which the pass
+      // does not write) instead of once per job
+      if (sh.in_f64 && sh.trans && !sh.db && cfg.ws && cfg.slices <= 4 && precut_default()) {
+        std::vector<GJob> pj;
+        std::vector<int> unit_pj(nu, -1);
+        bool ok = true;
+        for (size_t q = 0; q < vs.size() && ok; ++q) {
+          GJob& j = jobs[q];
+          const int u = vs[q].u;
+          const Plan& P = *units[u].plan;
+          const size_t cap = sizeof(float2) * (size_t)std::max(P.m + 2, std::max(P.p, 1)) * (size_t)P.PN;
+          ok = vs[q].in_tab && j.B0 == 1 && tc::precut_bytes(j.R, j.n, cfg.slices) <= cap;
+          if (!ok) break;
+          if (unit_pj[u] < 0) {
+            unit_pj[u] = (int)pj.size();
+            GJob c = j;
+            c.xslices = reinterpret_cast<const uint8_t*>(units[u].W2);
+            pj.push_back(c);
+          }
+          j.xslices = reinterpret_cast<const uint8_t*>(units[u].W2);
+        }
+        if (ok) {
+          B.precut_step(pj, cfg.slices);
+          sh.pc = true;
+        } else {
+          for (GJob& j : jobs) j.xslices = nullptr;
+        }
+      }
       B.mode_step(jobs, sh);
       if (sh.rr) {
         Step& stp = B.steps.back();
@@ -1190,6 +1244,15 @@ int seq_launch_all(Seq& S, cudaStream_t st) {
       F.ptrtab = S.dPtrtab;
       F.wait_ns = S.wait_ns;
       PK_RET(fused::launch(F, s.shape.slices, s.p, s.shape.grid, S.dStatus, st));
+    } else if (s.kind == STEP_PRECUT) {
+      GPass P;
+      P.jobs = S.dG + s.off;
+      P.njobs = s.count;
+      P.total_tiles = s.total;
+      P.ptrtab = S.dPtrtab;
+      P.wait_ns = S.wait_ns;
+      P.tmaps = nullptr;
+      PK_RET(tc::precut_pass(P, s.shape.slices, S.dStatus, st));
     } else if (s.kind == STEP_EXPSCAN) {
       launch_begin(KC_CONVERT, st);
       g_expscan_kernel<<<ew_grid(g_expscan_kernel, s.total), EW_THREADS, 0, st>>>(S.dE + s.off, s.count, s.total,

@@ -23,6 +23,8 @@ struct GJob {
   int n;                   // contracted size (E is n x n), multiple of 16, <= 4096
   int out_f64;
   int in_tab, out_tab;     // pointer-table entries, or -1
+  const uint8_t* xslices;  // the input's digit slices, cut once for all jobs that share it
+                           // ([128-fiber block][chunk32][slice] shared-memory images), or null
 };
 
 struct GPass {
@@ -43,6 +45,7 @@ struct PassShape {
   bool db;                 // double-buffered 128 x 64 tiles (needs n >= 64 in every job)
   bool rr;                 // warp-specialised kernel with the raw ring (float-float input,
                            // <= 4 slices, every job's input 16-byte aligned and direct)
+  bool pc;                 // float64 first pass from pre-cut input slices (GJob::xslices)
 };
 
 // Shared-memory operand layout of one 128-row x 32-K BF16 slice (8 KiB), K-major, used by the
@@ -63,6 +66,11 @@ struct PtrArgs {
 namespace tc {
 int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st);
 int set_ptrtab(void** tab, const PtrArgs& args, cudaStream_t st);
+// The digit slices of each job's float64 input (transposed first pass of a chain: B0 = 1),
+// cut once into job.xslices in the shared-memory image the mode kernel's MMAs read
+int precut_pass(const GPass& P, int slices, int* status, cudaStream_t st);
+// bytes of a job's pre-cut slices
+size_t precut_bytes(long long R, int n, int slices);
 // TMA tensor maps (128 bytes each, job order) of the inputs of a raw-ring mode pass's jobs
 // (boxes of `fibers` = 128 fibers for the warp-specialised kernel, 64 for the double-buffered one)
 int encode_raw_maps(const GJob* jobs, int njobs, bool trans, int fibers, uint8_t* out);

@@ -473,6 +473,7 @@ struct WsSlot {
   long long R, B0;
   long long base;        // TRANS: b0 * n * R (first element of the tile's slab); NORMAL: 0
   long long g0;          // first fiber of the tile: r0 (TRANS) or row0 (NORMAL)
+  const uint8_t* xsl;    // pre-cut input slices of the tile ([chunk][slice] images), or null
   int n, nsub, rb, eX, nrows_e, out_f64;
 };
 
@@ -596,6 +597,7 @@ __device__ __forceinline__ void ws_make_slot(const GPass& P, long long tile, int
   S.B0 = J.B0;
   S.base = TRANS ? (th / rtiles) * (long long)J.n * J.R : 0;
   S.g0 = TRANS ? (th % rtiles) * 128 : th * 128;
+  S.xsl = J.xslices ? J.xslices + (size_t)(th % rtiles) * (size_t)nsub * KS * SLICE_BYTES : nullptr;
   S.n = J.n;
   S.nsub = nsub;
   S.rb = rb;
@@ -758,9 +760,10 @@ __device__ __forceinline__ float ws_epi_cols(const WsSlot& S, uint32_t lane_base
   return mxf;
 }
 
-template <int KS, bool IN_F64, bool TRANS, bool RR = false>
+template <int KS, bool IN_F64, bool TRANS, bool RR = false, bool PC = false>
 __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
   static_assert(!RR || (!IN_F64 && KS <= 4), "raw ring: float-float passes up to 4 digit slices");
+  static_assert(!PC || (IN_F64 && TRANS && !RR), "pre-cut input: the float64 first pass");
   PK_CHECK_TABLES(P);
   const unsigned long long wl = P.wait_ns;  // limit of every bounded wait
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -790,7 +793,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
   const long long total_tiles = P.total_tiles;
   if (tid == 0) {
     for (int q = 0; q < NST; ++q) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_x[q])), "r"(WS_PROD));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_x[q])), "r"(PC ? 1 : WS_PROD));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_e[q])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[q])), "r"(WS_ISSUERS));
     }
@@ -905,7 +908,41 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       for (int k = e_last; k >= 0 && k >= e_last - (NST - 1); --k)
         mbar_wait(smem_u32(&full_e[k % NST]), ((uint32_t)k / NST) & 1u, CLEANUP_WAIT_NS);
     }
-  } else if (!RR && warp < WS_EPI0) {
+  } else if (PC && warp < WS_EPI0) {
+    // ------------------------------------------------------------ producers (pre-cut input)
+    // the input's digit slices were cut once for all jobs: thread 0 brings each chunk's X and E
+    // slices in by bulk copies; the other producer threads only read the slots
+    uint32_t it = 0, tc = 0;
+    int e_last = -1;
+    bool stop = false;
+    for (long long tile = blockIdx.x; tile < total_tiles && !stop; tile += gridDim.x, ++tc) {
+      WsSlot S;
+      if (!ws_get(slots, slot_full, slot_empty, tc, S, wl)) ws_fail(abort_s, status);
+      if (*abort_s) break;
+      if (tid != 0) continue;
+      for (int c = 0; c < S.nsub; ++c, ++it) {
+        const uint32_t st = it % NST, use = it / NST;
+        uint8_t* sX = smem + st * STAGE_BYTES;
+        uint8_t* sE = sX + HALF_BYTES;
+        if (use >= 1 && !mbar_wait(smem_u32(&empty[st]), (use - 1) & 1u, wl)) ws_fail(abort_s, status);
+        if (*abort_s) { stop = true; break; }
+        e_last = (int)it;
+        mbar_expect_tx(smem_u32(&full_e[st]), (uint32_t)HALF_BYTES);
+        bulk_copy_g2s(smem_u32(sE), PK_CK_SRC(S.ebase + (size_t)c * HALF_BYTES, HALF_BYTES, chk::SITE_MODE_ECOPY),
+                      (uint32_t)HALF_BYTES, smem_u32(&full_e[st]));
+        mbar_expect_tx(smem_u32(&full_x[st]), (uint32_t)HALF_BYTES);
+        bulk_copy_g2s(smem_u32(sX), PK_CK_SRC(S.xsl + (size_t)c * HALF_BYTES, HALF_BYTES, chk::SITE_MODE_LOAD),
+                      (uint32_t)HALF_BYTES, smem_u32(&full_x[st]));
+      }
+    }
+    if (tid == 0 && *abort_s) {
+      // bulk copies still in flight must land before the CTA's shared memory is released
+      for (int k = e_last; k >= 0 && k >= e_last - (NST - 1); --k) {
+        mbar_wait(smem_u32(&full_e[k % NST]), ((uint32_t)k / NST) & 1u, CLEANUP_WAIT_NS);
+        mbar_wait(smem_u32(&full_x[k % NST]), ((uint32_t)k / NST) & 1u, CLEANUP_WAIT_NS);
+      }
+    }
+  } else if (!RR && !PC && warp < WS_EPI0) {
     // ------------------------------------------------------------ producers
     const int orow = tid & 127;
     const int kh = tid >> 7;  // k-groups 2*kh, 2*kh + 1 of every 32-wide chunk
@@ -1144,6 +1181,61 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------- pre-cut input slices
+// One block per (job, 128-fiber block, 32-wide chunk): the digit slices of that chunk of the
+// job's float64 input (transposed first pass: B0 = 1, element (k, r) at k * R + r), cut as the
+// producers of the mode kernel cut them (same exponent, same integer digit cutting), written as
+// the KS shared-memory images [slice][8 KB] the MMAs read.  Blocks are counted by tile_begin.
+template <int KS>
+__global__ void __launch_bounds__(WS_PROD) precut_kernel(const __grid_constant__ GPass P) {
+  PK_CHECK_TABLES(P);
+  const int tid = threadIdx.x;
+  const int orow = tid & 127, kh = tid >> 7;
+  for (long long blk = blockIdx.x; blk < P.total_tiles; blk += gridDim.x) {
+    int lo = 0, hi = P.njobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.jobs[mid].tile_begin <= blk) lo = mid; else hi = mid - 1;
+    }
+    const GJob& J = P.jobs[lo];
+    const int nsub = (J.n + 31) / 32;
+    const long long jb = blk - J.tile_begin;
+    const long long rt = jb / nsub;
+    const int c = (int)(jb % nsub);
+    const double* in = static_cast<const double*>(job_in(P, J));
+    const int eb = 1011 + job_in_exp(J);
+    const long long g = rt * 128 + orow;
+    uint8_t* dst = const_cast<uint8_t*>(J.xslices) + (size_t)(rt * nsub + c) * KS * SLICE_BYTES;
+    double dv[16];   // all of this thread's loads in flight before any cutting
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int k = 32 * c + 16 * kh + e;
+      const double* src = in + (long long)k * J.R + g;
+      dv[e] = (g < J.R && k < J.n && PK_CK(src, sizeof(double), chk::SITE_MODE_LOAD)) ? __ldg(src) : 0.0;
+    }
+#pragma unroll
+    for (int g2 = 0; g2 < 2; ++g2) {
+      const double* d = dv + 8 * g2;
+      uint32_t pk[KS][4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        uint32_t s0, s1;
+        const uint64_t F0 = round_digits<KS>(fixed_f64(d[e], eb, s0));
+        const uint64_t F1 = round_digits<KS>(fixed_f64(d[e + 1], eb, s1));
+        uint32_t w[KS];
+        cut_pair<KS>(F0, s0, F1, s1, w);
+#pragma unroll
+        for (int sl = 0; sl < KS; ++sl) pk[sl][e >> 1] = w[sl];
+      }
+      const uint32_t off = chunk_offset(orow, 2 * kh + g2);
+#pragma unroll
+      for (int sl = 0; sl < KS; ++sl)
+        st_ck(reinterpret_cast<uint4*>(dst + sl * SLICE_BYTES + off), make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]),
+              chk::SITE_MODE_STORE);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- double-buffered variant
@@ -1698,7 +1790,7 @@ size_t smem_bytes(int ks, int sub) {
 }
 
 template <int KS, int SUB, bool IN_F64, bool TRANS>
-int launch_one(const GPass& P, int grid, bool ws, bool rr, int* status, cudaStream_t st) {
+int launch_one(const GPass& P, int grid, bool ws, bool rr, bool pc, int* status, cudaStream_t st) {
   // the warp-specialised kernel is built for 32-wide K chunks only (its 15 warps leave ~128
   // registers a thread, too few for the doubled raw-value buffers of 64-wide chunks)
   const bool use_ws = ws && SUB == 1;
@@ -1709,6 +1801,9 @@ int launch_one(const GPass& P, int grid, bool ws, bool rr, int* status, cudaStre
       kern = mode_kernel_ws<KS, false, TRANS, true>;
       sm = ws_smem_bytes_rr(KS);
     }
+  }
+  if constexpr (IN_F64 && TRANS && KS <= 4 && SUB == 1) {
+    if (use_ws && pc) kern = mode_kernel_ws<KS, true, true, false, true>;
   }
   const int threads = use_ws ? WS_THREADS : NTHREADS;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1724,12 +1819,13 @@ int launch_one(const GPass& P, int grid, bool ws, bool rr, int* status, cudaStre
 }
 
 template <int KS, int SUB>
-int launch_ks(const GPass& P, bool in_f64, bool trans, int grid, bool ws, bool rr, int* status, cudaStream_t st) {
+int launch_ks(const GPass& P, bool in_f64, bool trans, int grid, bool ws, bool rr, bool pc, int* status,
+              cudaStream_t st) {
   if (in_f64)
-    return trans ? launch_one<KS, SUB, true, true>(P, grid, ws, false, status, st)
-                 : launch_one<KS, SUB, true, false>(P, grid, ws, false, status, st);
-  return trans ? launch_one<KS, SUB, false, true>(P, grid, ws, rr, status, st)
-               : launch_one<KS, SUB, false, false>(P, grid, ws, rr, status, st);
+    return trans ? launch_one<KS, SUB, true, true>(P, grid, ws, false, pc, status, st)
+                 : launch_one<KS, SUB, true, false>(P, grid, ws, false, false, status, st);
+  return trans ? launch_one<KS, SUB, false, true>(P, grid, ws, rr, false, status, st)
+               : launch_one<KS, SUB, false, false>(P, grid, ws, rr, false, status, st);
 }
 
 template <int KS, bool IN_F64, bool TRANS>
@@ -1780,14 +1876,14 @@ int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) 
   }
   if (S.sub == 1) {
     switch (S.slices) {
-      case 3: return launch_ks<3, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, status, st);
-      case 4: return launch_ks<4, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, status, st);
-      case 5: return launch_ks<5, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, status, st);
-      case 6: return launch_ks<6, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, status, st);
+      case 3: return launch_ks<3, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, S.pc, status, st);
+      case 4: return launch_ks<4, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, S.pc, status, st);
+      case 5: return launch_ks<5, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, false, status, st);
+      case 6: return launch_ks<6, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, false, status, st);
       default: break;
     }
   } else if (S.sub == 2 && S.slices == 3) {
-    return launch_ks<3, 2>(P, S.in_f64, S.trans, grid, S.ws, false, status, st);
+    return launch_ks<3, 2>(P, S.in_f64, S.trans, grid, S.ws, false, false, status, st);
   }
   set_error("tc mode pass: unsupported (slices, sub-chunks) combination");
   return PHIKRON_EINVAL;
@@ -1837,6 +1933,32 @@ int encode_raw_maps(const GJob* jobs, int njobs, bool trans, int fibers, uint8_t
     if (r != CUDA_SUCCESS) return PHIKRON_ENOTSUP;
     std::memcpy(out + 128 * (size_t)j, &m, 128);
   }
+  return PHIKRON_OK;
+}
+
+size_t precut_bytes(long long R, int n, int slices) {
+  return (size_t)((R + 127) / 128) * (size_t)((n + 31) / 32) * (size_t)slices * SLICE_BYTES;
+}
+
+int precut_pass(const GPass& P, int slices, int* status, cudaStream_t st) {
+  (void)status;
+  if (P.njobs <= 0 || P.total_tiles <= 0) return PHIKRON_OK;
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<long long>(P.total_tiles, (long long)nsm * 4);
+  launch_begin(KC_CONVERT, st);
+  if (slices == 3) {
+    precut_kernel<3><<<grid, WS_PROD, 0, st>>>(P);
+  } else if (slices == 4) {
+    precut_kernel<4><<<grid, WS_PROD, 0, st>>>(P);
+  } else {
+    launch_end(st);
+    set_error("pre-cut input: 3 or 4 digit slices");
+    return PHIKRON_EINVAL;
+  }
+  launch_end(st);
+  PK_CHECK_LAUNCH();
   return PHIKRON_OK;
 }
 
