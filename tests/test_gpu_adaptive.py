@@ -61,7 +61,8 @@ def test_adaptive_rejects_mixed_path():
 
 def test_adaptive_convdiff3d_128_against_stored_oracle_samples():
     """The 128^3 convection-diffusion workload against the stored O3 samples (sampled relative
-    error normalised like the full 2-norm: rms(diff) / rms(phi_l))."""
+    error normalised like the full 2-norm: rms(diff) / rms(phi_l)), gated at 1e-10, the
+    float64 path's accuracy target on this workload."""
     import os
     import sys
     sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
@@ -76,6 +77,7 @@ def test_adaptive_convdiff3d_128_against_stored_oracle_samples():
     for l in range(prob.l_max + 1):
         d = out[l][idx] - vals[l]
         err = np.sqrt(np.mean(d * d)) / (norm2[l] / np.sqrt(prob.N))
-        assert err <= 1e-9, (l, err, info["adaptive_nodes"])
+        print(f"phi_{l}: sampled relative error {err:.3e}")
+        assert err <= 1e-10, (l, err, info["adaptive_nodes"])
     print(f"adaptive CC 128^3: s={info['s']} nodes={info['adaptive_nodes']} err={info['adaptive_err']:.2e}")
     plan.close()
