@@ -49,6 +49,30 @@ def test_noalloc_matches_allocating_entry_point_twice(shape):
         assert np.max(np.abs(o - r)) <= 1e-12 * np.max(np.abs(r)), call
 
 
+def test_noalloc_call_after_the_first_takes_no_device_memory():
+    """After a first call on the device (which may load the library's kernels and place its
+    built-in array), a call leaves the device's free memory unchanged: it allocates nothing."""
+    L, B = _lib()
+    shape = (32, 48, 40)
+    ns = (C.c_int * 3)(*shape)
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(5)
+    mats = [torch.from_numpy(rng.standard_normal((n, n)) / n).cuda() for n in shape]
+    v = torch.from_numpy(rng.standard_normal(N)).cuda()
+    out = torch.empty_like(v)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.phikron_kron_apply_f64_noalloc(3, ns, _ptrs(mats), v.data_ptr(), out.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    first = out.clone()
+    free_before = torch.cuda.mem_get_info()[0]
+    rc = L.phikron_kron_apply_f64_noalloc(3, ns, _ptrs(mats), v.data_ptr(), out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free_after = torch.cuda.mem_get_info()[0]
+    assert rc == 0, L.phikron_last_error()
+    assert free_after == free_before, (free_before, free_after)
+    assert torch.equal(out, first)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     L, B = _lib()
     cap = L.phikron_noalloc_max_elements()
