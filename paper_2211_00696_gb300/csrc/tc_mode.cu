@@ -771,6 +771,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
   constexpr int STAGE_BYTES = 2 * HALF_BYTES;
   constexpr int NST = RR ? WS_RR_STAGES : ws_stages(KS);
   constexpr int NRAW = RR ? WS_NRAW : 0;
+  constexpr int NRAW_DIV = RR ? WS_NRAW : 1;   // ring index arithmetic (compiled, unused, without the ring)
   uint8_t* rawring = smem + NST * STAGE_BYTES;   // [NRAW] raw chunks (raw-ring variant)
   uint8_t* tail = rawring + NRAW * WS_RAW_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
@@ -837,7 +838,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
       const int nr = (int)min(128LL, TRANS ? S.R - S.g0 : S.B0 - S.g0);   // valid fibers of the tile
       for (int c = 0; c < S.nsub; ++c, ++it) {
         const uint32_t st = it % NST, use = it / NST;
-        const uint32_t r = it % NRAW, ru = it / NRAW;
+        const uint32_t r = it % NRAW_DIV, ru = it / NRAW_DIV;
         uint8_t* sX = smem + st * STAGE_BYTES;
         uint8_t* sE = sX + HALF_BYTES;
         const uint8_t* rb = rawring + r * WS_RAW_BYTES;
@@ -1152,7 +1153,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
         mbar_arrive(smem_u32(&slot_full[q]));
       }
       for (int c = 0; c < L.nsub; ++c, ++it) {
-        const uint32_t r = it % NRAW, ru = it / NRAW;
+        const uint32_t r = it % NRAW_DIV, ru = it / NRAW_DIV;
         ok = ru == 0 || mbar_wait(smem_u32(&raw_empty[r]), (ru - 1) & 1u, wl);
         if (!ok) ws_fail(abort_s, status);
         if (__any_sync(0xffffffffu, !ok || *abort_s)) { stop = true; break; }
@@ -1163,7 +1164,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
     if (lane == 0 && *abort_s) {
       // raw copies still in flight must land before the CTA's shared memory is released
       for (long long k = r_last; k >= 0 && k >= r_last - (NRAW - 1); --k)
-        mbar_wait(smem_u32(&raw_full[k % NRAW]), (uint32_t)(k / NRAW) & 1u, CLEANUP_WAIT_NS);
+        mbar_wait(smem_u32(&raw_full[k % NRAW_DIV]), (uint32_t)(k / NRAW_DIV) & 1u, CLEANUP_WAIT_NS);
     }
   } else if (!RR && warp == WS_SCHED && lane == 0) {
     // ------------------------------------------------------------ scheduler (warp 13, lane 0)
@@ -1295,7 +1296,7 @@ template <bool IN_F64, bool TRANS>
 __device__ __forceinline__ void db_load(const WsSlot& S, int fib, int kc, Raw<IN_F64>& raw) {
   const long long gr = S.g0 + fib;
   const bool vr = TRANS ? (gr < S.R) : (gr < S.B0);
-  if (!TRANS && !IN_F64) {
+  if constexpr (!TRANS && !IN_F64) {
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
       const int k = kc + e;
@@ -1305,17 +1306,17 @@ __device__ __forceinline__ void db_load(const WsSlot& S, int fib, int kc, Raw<IN
       raw.f[e] = make_float2(v.x, v.y);
       raw.f[e + 1] = make_float2(v.z, v.w);
     }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    const int k = kc + e;
-    const long long idx = TRANS ? S.base + (long long)k * S.R + gr : gr * (long long)S.n + k;
-    const bool ok = vr && k < S.n && PK_CK((const char*)S.in + 8 * idx, 8, chk::SITE_MODE_LOAD);
-    if (IN_F64)
-      raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(S.in) + idx) : 0.0;
-    else
-      raw.f[e] = ok ? __ldg(reinterpret_cast<const float2*>(S.in) + idx) : make_float2(0.f, 0.f);
+    for (int e = 0; e < 8; ++e) {
+      const int k = kc + e;
+      const long long idx = TRANS ? S.base + (long long)k * S.R + gr : gr * (long long)S.n + k;
+      const bool ok = vr && k < S.n && PK_CK((const char*)S.in + 8 * idx, 8, chk::SITE_MODE_LOAD);
+      if constexpr (IN_F64)
+        raw.d[e] = ok ? __ldg(reinterpret_cast<const double*>(S.in) + idx) : 0.0;
+      else
+        raw.f[e] = ok ? __ldg(reinterpret_cast<const float2*>(S.in) + idx) : make_float2(0.f, 0.f);
+    }
   }
 }
 
@@ -1362,6 +1363,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
   constexpr int STAGE = XBYTES + KS * SLICE_BYTES;
   constexpr int NST = RR ? WS_RR_STAGES : db_stages(KS);
   constexpr int NRAW = RR ? WS_NRAW : 0;
+  constexpr int NRAW_DIV = RR ? WS_NRAW : 1;   // ring index arithmetic (compiled, unused, without the ring)
   uint8_t* staging = smem + NST * STAGE;
   uint8_t* rawring = staging + DB_STAGE_BYTES;   // [NRAW] raw chunks (raw-ring variant)
   uint8_t* tail = rawring + NRAW * DB_RAW_BYTES;
@@ -1430,7 +1432,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
       const int nr = (int)min(64LL, TRANS ? S.R - S.g0 : S.B0 - S.g0);   // valid fibers of the tile
       for (int c = 0; c < S.nsub; ++c, ++it) {
         const uint32_t st = it % NST, use = it / NST;
-        const uint32_t r = it % NRAW, ru = it / NRAW;
+        const uint32_t r = it % NRAW_DIV, ru = it / NRAW_DIV;
         uint8_t* sX = smem + st * STAGE;
         uint8_t* sE = sX + XBYTES;
         const uint8_t* rb = rawring + r * DB_RAW_BYTES;
@@ -1747,7 +1749,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
         mbar_arrive(smem_u32(&slot_full[q]));
       }
       for (int c = 0; c < L.nsub; ++c, ++it) {
-        const uint32_t r = it % NRAW, ru = it / NRAW;
+        const uint32_t r = it % NRAW_DIV, ru = it / NRAW_DIV;
         ok = ru == 0 || mbar_wait(smem_u32(&raw_empty[r]), (ru - 1) & 1u, wl);
         if (!ok) ws_fail(abort_s, status);
         if (__any_sync(0xffffffffu, !ok || *abort_s)) { stop = true; break; }
@@ -1758,7 +1760,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_db(const __grid_con
     if (lane == 0 && *abort_s) {
       // raw copies still in flight must land before the CTA's shared memory is released
       for (long long k = r_last; k >= 0 && k >= r_last - (NRAW - 1); --k)
-        mbar_wait(smem_u32(&raw_full[k % NRAW]), (uint32_t)(k / NRAW) & 1u, CLEANUP_WAIT_NS);
+        mbar_wait(smem_u32(&raw_full[k % NRAW_DIV]), (uint32_t)(k / NRAW_DIV) & 1u, CLEANUP_WAIT_NS);
     }
   } else if (!RR && warp == WS_SCHED && lane == 0) {
     // ------------------------------------------------------------ scheduler (64-fiber tiles)
@@ -1903,7 +1905,7 @@ int encode_raw_maps(const GJob* jobs, int njobs, bool trans, int fibers, uint8_t
     looked = true;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       encode = reinterpret_cast<EncodeTiled>(fn);
     cudaGetLastError();
