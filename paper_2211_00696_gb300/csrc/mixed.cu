@@ -956,13 +956,14 @@ int seq_build(Seq& S, std::vector<SeqUnit>& units, int ninst, const SeqConfig& c
       for (const GJob& j : jobs)
         direct16 = direct16 && j.in_tab < 0 && (reinterpret_cast<uintptr_t>(j.in) & 15u) == 0 && j.n % 16 == 0 &&
                    (!trans || j.R % 16 == 0);
-      sh.rr = cfg.rr && (cfg.ws || sh.db) && !sh.in_f64 && cfg.slices <= 4 && direct16;
+      // (the warp-specialised raw-ring kernel up to 5 slices, the double-buffered one up to 4)
+      sh.rr = cfg.rr && (sh.db ? cfg.slices <= 4 : (cfg.ws && cfg.slices <= 5)) && !sh.in_f64 && direct16;
       if (dims == 1) sh.trans = false;
       // all jobs of one pass share the formulation (same axis d)
       // the float64 first pass of a chain whose vectors share their unit's input: that input's
       // digit slices are cut once per unit (into the unit's second work buffer, which the pass
       // does not write) instead of once per job
-      if (sh.in_f64 && sh.trans && !sh.db && cfg.ws && cfg.slices <= 4 && precut_default()) {
+      if (sh.in_f64 && sh.trans && !sh.db && cfg.ws && precut_default()) {
         std::vector<GJob> pj;
         std::vector<int> unit_pj(nu, -1);
         bool ok = true;

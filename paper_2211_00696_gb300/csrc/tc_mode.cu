@@ -499,12 +499,15 @@ size_t ws_smem_bytes(int ks) {
 // With loads issued by the producers themselves, one prefetched chunk (32 KB per SM, the
 // register budget) at ~1.5 us of loaded latency capped the input near half the HBM bandwidth.
 constexpr int WS_NRAW = 3;
+// raw buffers of the warp-specialised kernel's ring: three up to 4 digit slices, two at 5
+// (two 80 KB operand stages leave room for two)
+__host__ __device__ constexpr int ws_nraw(int ks) { return ks <= 4 ? WS_NRAW : 2; }
 constexpr int WS_RAW_BYTES = 128 * KC * 8;
 constexpr int WS_RR_STAGES = 2;
 static_assert(3 * WS_RR_STAGES + 3 + 2 * WS_SLOTS + 2 * WS_NRAW <= WS_BAR_BYTES / 8, "mbarrier area (raw ring)");
 
 size_t ws_smem_bytes_rr(int ks) {
-  return (size_t)WS_RR_STAGES * 2 * ks * SLICE_BYTES + (size_t)WS_NRAW * WS_RAW_BYTES + WS_BAR_BYTES + WS_SCALE_BYTES +
+  return (size_t)WS_RR_STAGES * 2 * ks * SLICE_BYTES + (size_t)ws_nraw(ks) * WS_RAW_BYTES + WS_BAR_BYTES + WS_SCALE_BYTES +
          WS_SLOT_BYTES + 32;
 }
 
@@ -762,7 +765,7 @@ __device__ __forceinline__ float ws_epi_cols(const WsSlot& S, uint32_t lane_base
 
 template <int KS, bool IN_F64, bool TRANS, bool RR = false, bool PC = false>
 __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_constant__ GPass P, int* status) {
-  static_assert(!RR || (!IN_F64 && KS <= 4), "raw ring: float-float passes up to 4 digit slices");
+  static_assert(!RR || (!IN_F64 && KS <= 5), "raw ring: float-float passes up to 5 digit slices");
   static_assert(!PC || (IN_F64 && TRANS && !RR), "pre-cut input: the float64 first pass");
   PK_CHECK_TABLES(P);
   const unsigned long long wl = P.wait_ns;  // limit of every bounded wait
@@ -770,8 +773,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mode_kernel_ws(const __grid_con
   constexpr int HALF_BYTES = KS * SLICE_BYTES;
   constexpr int STAGE_BYTES = 2 * HALF_BYTES;
   constexpr int NST = RR ? WS_RR_STAGES : ws_stages(KS);
-  constexpr int NRAW = RR ? WS_NRAW : 0;
-  constexpr int NRAW_DIV = RR ? WS_NRAW : 1;   // ring index arithmetic (compiled, unused, without the ring)
+  constexpr int NRAW = RR ? ws_nraw(KS) : 0;
+  constexpr int NRAW_DIV = RR ? ws_nraw(KS) : 1;   // ring index arithmetic (compiled, unused, without the ring)
   uint8_t* rawring = smem + NST * STAGE_BYTES;   // [NRAW] raw chunks (raw-ring variant)
   uint8_t* tail = rawring + NRAW * WS_RAW_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
@@ -1798,13 +1801,13 @@ int launch_one(const GPass& P, int grid, bool ws, bool rr, bool pc, int* status,
   const bool use_ws = ws && SUB == 1;
   size_t sm = use_ws ? ws_smem_bytes(KS) : smem_bytes(KS, SUB);
   auto kern = use_ws ? mode_kernel_ws<KS, IN_F64, TRANS> : mode_kernel<KS, SUB, IN_F64, TRANS>;
-  if constexpr (!IN_F64 && KS <= 4 && SUB == 1) {
+  if constexpr (!IN_F64 && KS <= 5 && SUB == 1) {
     if (use_ws && rr) {
       kern = mode_kernel_ws<KS, false, TRANS, true>;
       sm = ws_smem_bytes_rr(KS);
     }
   }
-  if constexpr (IN_F64 && TRANS && KS <= 4 && SUB == 1) {
+  if constexpr (IN_F64 && TRANS && SUB == 1) {
     if (use_ws && pc) kern = mode_kernel_ws<KS, true, true, false, true>;
   }
   const int threads = use_ws ? WS_THREADS : NTHREADS;
@@ -1954,9 +1957,13 @@ int precut_pass(const GPass& P, int slices, int* status, cudaStream_t st) {
     precut_kernel<3><<<grid, WS_PROD, 0, st>>>(P);
   } else if (slices == 4) {
     precut_kernel<4><<<grid, WS_PROD, 0, st>>>(P);
+  } else if (slices == 5) {
+    precut_kernel<5><<<grid, WS_PROD, 0, st>>>(P);
+  } else if (slices == 6) {
+    precut_kernel<6><<<grid, WS_PROD, 0, st>>>(P);
   } else {
     launch_end(st);
-    set_error("pre-cut input: 3 or 4 digit slices");
+    set_error("pre-cut input: 3 to 6 digit slices");
     return PHIKRON_EINVAL;
   }
   launch_end(st);
