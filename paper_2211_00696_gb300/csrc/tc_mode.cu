@@ -1883,8 +1883,8 @@ int mode_pass(const GPass& P, const PassShape& S, int* status, cudaStream_t st) 
     switch (S.slices) {
       case 3: return launch_ks<3, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, S.pc, status, st);
       case 4: return launch_ks<4, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, S.pc, status, st);
-      case 5: return launch_ks<5, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, false, status, st);
-      case 6: return launch_ks<6, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, false, status, st);
+      case 5: return launch_ks<5, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, S.pc, status, st);
+      case 6: return launch_ks<6, 1>(P, S.in_f64, S.trans, grid, S.ws, rr, S.pc, status, st);
       default: break;
     }
   } else if (S.sub == 2 && S.slices == 3) {
