@@ -149,7 +149,7 @@ def peaks():
 # profiles/mode_kernel_ws_convdiff3d_n128_ncu_full.md (one launch of the z-mode node pass:
 # 11 vectors x N unknowns); valid only while the kernel code is the one captured (hash of
 # tc_mode.cu without comments and blank lines, see code_hash).
-PROFILED_MODE_TRAFFIC = {"source_sha256_16": "9401698783cb60f9", "bytes": 186.084352e6 + 128.035328e6,
+PROFILED_MODE_TRAFFIC = {"source_sha256_16": "29768ebe00cf63a1", "bytes": 186.086144e6 + 126.577664e6,
                          "vector_passes": 11, "N": 2097152}
 
 
