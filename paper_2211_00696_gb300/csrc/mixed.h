@@ -43,8 +43,8 @@ struct PassShape {
   bool in_f64, trans;
   bool ws;                 // warp-specialised kernel (producer / MMA / epilogue warps)
   bool db;                 // double-buffered 128 x 64 tiles (needs n >= 64 in every job)
-  bool rr;                 // warp-specialised kernel with the raw ring (float-float input,
-                           // <= 4 slices, every job's input 16-byte aligned and direct)
+  bool rr;                 // raw-ring kernel (float-float input, every job's input 16-byte
+                           // aligned and direct; <= 5 slices warp-specialised, <= 4 double-buffered)
   bool pc;                 // float64 first pass from pre-cut input slices (GJob::xslices)
 };
 

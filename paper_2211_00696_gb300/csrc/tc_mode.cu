@@ -492,9 +492,9 @@ size_t ws_smem_bytes(int ks) {
   return (size_t)ws_stages(ks) * 2 * ks * SLICE_BYTES + WS_BAR_BYTES + WS_SCALE_BYTES + WS_SLOT_BYTES + 32;
 }
 
-// Raw-ring variant (float-float passes up to 4 digit slices): the raw float-float operand of a
-// 32-wide chunk (128 fibers x 32 K x 8 B = 32 KB) arrives in shared memory by bulk copies that
-// the scheduler warp issues up to WS_NRAW chunks ahead, so that ~96 KB per SM are in flight
+// Raw-ring variant (float-float passes up to 5 digit slices): the raw float-float operand of a
+// 32-wide chunk (128 fibers x 32 K x 8 B = 32 KB) arrives in shared memory by TMA tensor copies
+// that the scheduler warp issues up to ws_nraw chunks ahead, so that ~96 KB per SM are in flight
 // without holding registers; the producers cut from shared memory into two operand stages.
 // With loads issued by the producers themselves, one prefetched chunk (32 KB per SM, the
 // register budget) at ~1.5 us of loaded latency capped the input near half the HBM bandwidth.
